@@ -1,0 +1,129 @@
+"""FP64 CPU oracle for the 3D wide-angle PE range march (ctypes wrapper).
+
+TEST INFRASTRUCTURE ONLY.  The oracle is the plain, slow, obviously correct
+reference the CUDA library is checked against (paper Eq. 4-8, Fig. 2; the C
+source states each reading taken).  Only the tests, the smoke check and the
+benchmark's CPU-baseline leg may import this package; the library never does.
+
+Pinning status (what fixes each function other than itself): the tridiagonal
+and cyclic solvers are pinned to LAPACK via numpy.linalg.solve and to the
+circulant FFT solution; the step is pinned to a dense LU solve of the printed
+Eq. 4 on tiny grids, to the closed-form discrete eigenmode multipliers, to
+exact norm conservation, to reversibility, to the theta-uniform reduction and
+to mirror symmetry (tests/test_oracle_pins.py).  No value printed in the
+paper pins it: the paper prints no field values (parity to the paper's own
+outputs is unpinned).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pe3d_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+CFLAGS = ["-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp"]
+
+
+def build(src: str = _SRC, out: str = _LIB, extra: list[str] | None = None) -> str:
+    """Compile the oracle with gcc (plain C99, no FMA contraction, OpenMP)."""
+    cmd = ["gcc", *CFLAGS, *(extra or []), src, "-o", out, "-lm"]
+    subprocess.run(cmd, check=True, capture_output=True, text=True)
+    return out
+
+
+def _needs_build(src: str, out: str) -> bool:
+    return not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src)
+
+
+class OracleLib:
+    """Typed handle on one compiled oracle shared object."""
+
+    def __init__(self, path: str):
+        self.path = path
+        L = ctypes.CDLL(path)
+        P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.oracle_tridiag_solve.argtypes = [I, P, P, P, P]
+        L.oracle_cyclic_solve.argtypes = [I, P, P, P, P]
+        L.oracle_step.argtypes = [I, I, D, D, D, D, D, I, P, P, I]
+        L.oracle_march.argtypes = [I, I, D, D, D, D, I, P, P, I, P, D, I, I, P, I]
+        for f in ("oracle_tridiag_solve", "oracle_cyclic_solve", "oracle_step", "oracle_march"):
+            getattr(L, f).restype = I
+        self.L = L
+
+    @staticmethod
+    def _c128(a):
+        return np.ascontiguousarray(a, dtype=np.complex128)
+
+    def tridiag_solve(self, sub, diag, sup, b):
+        sub, diag, sup = self._c128(sub), self._c128(diag), self._c128(sup)
+        x = self._c128(b).copy()
+        rc = self.L.oracle_tridiag_solve(len(x), sub.ctypes.data, diag.ctypes.data,
+                                         sup.ctypes.data, x.ctypes.data)
+        if rc:
+            raise RuntimeError(f"oracle_tridiag_solve failed ({rc})")
+        return x
+
+    def cyclic_solve(self, sub, diag, sup, b):
+        sub, diag, sup = self._c128(sub), self._c128(diag), self._c128(sup)
+        x = self._c128(b).copy()
+        rc = self.L.oracle_cyclic_solve(len(x), sub.ctypes.data, diag.ctypes.data,
+                                        sup.ctypes.data, x.ctypes.data)
+        if rc:
+            raise RuntimeError(f"oracle_cyclic_solve failed ({rc})")
+        return x
+
+    def step(self, u, n2, *, dz, dtheta, dr, k0, rstar, periodic, nthreads=1):
+        u = self._c128(u).copy()
+        n2 = self._c128(n2)
+        Nt, Nz = u.shape
+        rc = self.L.oracle_step(Nz, Nt, dz, dtheta, dr, k0, rstar, int(periodic),
+                                n2.ctypes.data, u.ctypes.data, int(nthreads))
+        if rc:
+            raise RuntimeError(f"oracle_step failed ({rc})")
+        return u
+
+    def march(self, grid, n2, slice_r, u0, *, steps=None, stride=None, r0=None, nthreads=None):
+        steps = grid.steps if steps is None else steps
+        stride = grid.stride if stride is None else stride
+        r0 = grid.r0 if r0 is None else r0
+        nthreads = default_threads() if nthreads is None else nthreads
+        n2 = self._c128(n2)
+        slice_r = np.ascontiguousarray(slice_r, dtype=np.float64)
+        u0 = self._c128(u0)
+        Nt, Nz = u0.shape
+        n_out = steps // stride
+        out = np.zeros((max(n_out, 1), Nt, Nz), np.complex128)
+        rc = self.L.oracle_march(Nz, Nt, grid.dz, grid.dtheta, grid.dr, grid.k0, int(grid.periodic),
+                                 n2.ctypes.data, slice_r.ctypes.data, len(slice_r), u0.ctypes.data,
+                                 float(r0), int(steps), int(stride), out.ctypes.data, int(nthreads))
+        if rc:
+            raise RuntimeError(f"oracle_march failed ({rc})")
+        return out[:n_out]
+
+
+def default_threads() -> int:
+    return max(1, len(os.sched_getaffinity(0)))
+
+
+def load() -> OracleLib:
+    """Build (if stale) and load the oracle."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if _needs_build(_SRC, _LIB):
+                build()
+            _lib = OracleLib(_LIB)
+        return _lib
+
+
+def march_workload(wl, **kw):
+    """Oracle march of a workloads.Workload."""
+    return load().march(wl.grid, wl.n2, wl.slice_r, wl.u0, **kw)

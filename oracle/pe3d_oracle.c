@@ -1,0 +1,343 @@
+/*
+ * pe3d_oracle.c -- plain FP64 CPU oracle for the range march of the 3D
+ * wide-angle parabolic equation (Xu, Wang, Chronopoulos, Yue, "Performance
+ * Optimization and Parallelization of a Parabolic Equation Solver in
+ * Computational Ocean Acoustics on Modern Many-core Computer", Sec. 2.1).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously correct
+ * reference that the CUDA library is checked against.  Only the tests, the
+ * smoke check and the benchmark's CPU-baseline leg may build or call it; the
+ * library never links it, and it shares no code with the library.
+ *
+ * What it computes (paper Eq. 4 and the two-step procedure of Eq. 5-8, in the
+ * order of the loop in Fig. 2):
+ *
+ *   [1 + (1/4 - d/4) X][1 - (d/4) Y] u^{j+1} = [1 + (1/4 + d/4) X][1 + (d/4) Y] u^j,
+ *   d = i k0 dr,
+ *
+ * with, on the grid u[m][l] (m: azimuth, l: depth, depth z_l = (l+1) dz):
+ *
+ *   (X u)[m][l] = (n^2[m][l] - 1) u[m][l] + s (u[m][l+1] - 2 u[m][l] + u[m][l-1]),
+ *                 s = 1 / (k0 dz)^2, ghosts u[m][-1] = u[m][Nz] = 0;
+ *   (Y u)[m][l] = c (u[m+1][l] - 2 u[m][l] + u[m-1][l]),
+ *                 c = 1 / (k0 r* dtheta)^2, walled ghosts u[-1] = u[Ntheta] = 0,
+ *                 or m +- 1 taken modulo Ntheta for a full circle.
+ *
+ * Readings taken where the paper is silent or garbled:
+ *   - X uses (n^2 - 1) + d^2/dz^2 / k0^2 (the printed k0^2 (n^2 - 1) term is
+ *     dimensionally inconsistent with Eq. 2 divided by k0^2);
+ *   - both sides of Eq. 4 use the operators at r* = r_{j+1}: Fig. 2 advances r
+ *     before it updates A and B;
+ *   - the medium is piecewise constant in range: slice k is active for
+ *     R_k <= r* < R_{k+1} (slice 0 before R_0);
+ *   - the full-circle azimuth system (cyclic) is solved with the Sherman-
+ *     Morrison formula around a tridiagonal solve.
+ *
+ * The step, as Eq. 4 and Eq. 5/6 order it:
+ *   1. w   = [1 + (d/4) Y] u^j            (rightmost factor of the RHS first)
+ *   2. RHS = [1 + (1/4 + d/4) X] w
+ *   3. v   : [1 + (1/4 - d/4) X] v = RHS, one tridiagonal system in l per m  (Eq. 5, 7)
+ *   4. u^{j+1}: [1 - (d/4) Y] u^{j+1} = v, one system in m per l            (Eq. 6, 8)
+ *
+ * Systems are solved by textbook Gaussian elimination with partial pivoting on
+ * the tridiagonal band (row interchanges, one fill-in superdiagonal), written
+ * here rather than called from a library.
+ *
+ * Complex numbers: C99 double complex.  Build with -ffp-contract=off so that
+ * every product and sum is rounded as written.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+enum { OR_OK = 0, OR_ERR_ARG = -1, OR_ERR_SINGULAR = -3, OR_ERR_OOM = -2 };
+
+/* ------------------------------------------------------------------------ */
+/* Tridiagonal Gaussian elimination with partial pivoting.
+ *
+ * Row i of the system:  sub[i] x[i-1] + diag[i] x[i] + sup[i] x[i+1] = b[i]
+ * (sub[0] and sup[n-1] are ignored).  b is overwritten with x.
+ * Work arrays (length n each) are caller-supplied so the routine allocates
+ * nothing.  Returns OR_ERR_SINGULAR on an exactly zero pivot.            */
+static int tridiag_gepp(int n, const cplx *sub, const cplx *diag, const cplx *sup,
+                        cplx *b, cplx *d, cplx *u1, cplx *u2)
+{
+    if (n <= 0) return OR_OK;
+    /* d: current diagonal, u1: first superdiagonal, u2: fill-in second superdiagonal */
+    for (int i = 0; i < n; ++i) {
+        d[i] = diag[i];
+        u1[i] = (i + 1 < n) ? sup[i] : 0.0;
+        u2[i] = 0.0;
+    }
+    for (int i = 0; i + 1 < n; ++i) {
+        cplx below = sub[i + 1];             /* entry (i+1, i) */
+        if (cabs(d[i]) >= cabs(below)) {
+            /* no interchange: eliminate (i+1, i) with row i */
+            if (d[i] == 0.0) return OR_ERR_SINGULAR;
+            cplx mult = below / d[i];
+            d[i + 1] = d[i + 1] - mult * u1[i];
+            /* row i has no entry in column i+2 (u2[i] is still zero) */
+            b[i + 1] = b[i + 1] - mult * b[i];
+        } else {
+            /* interchange rows i and i+1, then eliminate */
+            cplx mult = d[i] / below;
+            cplx r_i1 = d[i + 1];                          /* old (i+1, i+1) */
+            cplx r_i2 = (i + 2 < n) ? u1[i + 1] : 0.0;     /* old (i+1, i+2) */
+            cplx o_i1 = u1[i];                             /* old (i, i+1)   */
+            d[i] = below;
+            u1[i] = r_i1;
+            u2[i] = r_i2;
+            d[i + 1] = o_i1 - mult * r_i1;
+            if (i + 2 < n) u1[i + 1] = 0.0 - mult * r_i2;
+            cplx bi = b[i];
+            b[i] = b[i + 1];
+            b[i + 1] = bi - mult * b[i];
+        }
+    }
+    if (d[n - 1] == 0.0) return OR_ERR_SINGULAR;
+    /* back substitution with the (up to) two superdiagonals */
+    b[n - 1] = b[n - 1] / d[n - 1];
+    if (n >= 2) b[n - 2] = (b[n - 2] - u1[n - 2] * b[n - 1]) / d[n - 2];
+    for (int i = n - 3; i >= 0; --i)
+        b[i] = (b[i] - u1[i] * b[i + 1] - u2[i] * b[i + 2]) / d[i];
+    return OR_OK;
+}
+
+/* Exported for the tests: solve one tridiagonal system (x: rhs in, solution out). */
+int oracle_tridiag_solve(int n, const cplx *sub, const cplx *diag, const cplx *sup, cplx *x)
+{
+    if (n < 0) return OR_ERR_ARG;
+    if (n == 0) return OR_OK;
+    cplx *w = (cplx *)malloc(sizeof(cplx) * 3 * (size_t)n);
+    if (!w) return OR_ERR_OOM;
+    int rc = tridiag_gepp(n, sub, diag, sup, x, w, w + n, w + 2 * n);
+    free(w);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cyclic (periodic) tridiagonal system by the Sherman-Morrison formula.
+ *
+ * Row i:  sub[i] x[i-1 mod n] + diag[i] x[i] + sup[i] x[i+1 mod n] = b[i].
+ * The periodic matrix is C = T + u v^T with
+ *   gamma = -diag[0],  u = (gamma, 0, ..., 0, sup[n-1])^T,
+ *   v = (1, 0, ..., 0, sub[0] / gamma)^T,
+ * where T is C with its two corners removed and its first and last diagonal
+ * entries replaced by diag[0] - gamma and diag[n-1] - sup[n-1] sub[0] / gamma.
+ * Then x = y - (v.y / (1 + v.z)) z with T y = b and T z = u.
+ * n = 1 collapses to one equation (sub + diag + sup) x = b.
+ * work: 6 n complex numbers.                                             */
+static int cyclic_sm(int n, const cplx *sub, const cplx *diag, const cplx *sup,
+                     cplx *b, cplx *work)
+{
+    if (n <= 0) return OR_OK;
+    if (n == 1) {
+        cplx a = sub[0] + diag[0] + sup[0];
+        if (a == 0.0) return OR_ERR_SINGULAR;
+        b[0] = b[0] / a;
+        return OR_OK;
+    }
+    cplx *tdiag = work, *z = work + n, *d = work + 2 * n, *u1 = work + 3 * n, *u2 = work + 4 * n;
+    cplx *tsub = work + 5 * n;   /* T's sub-diagonal: C's, without the corner */
+    cplx gamma = -diag[0];
+    cplx corner_tr = sub[0];       /* C[0][n-1]  */
+    cplx corner_bl = sup[n - 1];   /* C[n-1][0]  */
+    for (int i = 0; i < n; ++i) {
+        tdiag[i] = diag[i];
+        tsub[i] = (i > 0) ? sub[i] : 0.0;
+        z[i] = 0.0;
+    }
+    tdiag[0] = diag[0] - gamma;
+    tdiag[n - 1] = diag[n - 1] - corner_bl * corner_tr / gamma;
+    z[0] = gamma;
+    z[n - 1] = corner_bl;
+    int rc = tridiag_gepp(n, tsub, tdiag, sup, b, d, u1, u2);   /* b <- y */
+    if (rc) return rc;
+    rc = tridiag_gepp(n, tsub, tdiag, sup, z, d, u1, u2);       /* z <- T^-1 u */
+    if (rc) return rc;
+    cplx vy = b[0] + (corner_tr / gamma) * b[n - 1];
+    cplx vz = z[0] + (corner_tr / gamma) * z[n - 1];
+    cplx den = 1.0 + vz;
+    if (den == 0.0) return OR_ERR_SINGULAR;
+    cplx f = vy / den;
+    for (int i = 0; i < n; ++i) b[i] = b[i] - f * z[i];
+    return OR_OK;
+}
+
+int oracle_cyclic_solve(int n, const cplx *sub, const cplx *diag, const cplx *sup, cplx *x)
+{
+    if (n < 0) return OR_ERR_ARG;
+    if (n == 0) return OR_OK;
+    cplx *w = (cplx *)malloc(sizeof(cplx) * 6 * (size_t)n);
+    if (!w) return OR_ERR_OOM;
+    int rc = cyclic_sm(n, sub, diag, sup, x, w);
+    free(w);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The discrete operators of Eq. 4, row by row.                            */
+
+/* Row l of X for azimuth m: coefficients of u[m][l-1], u[m][l], u[m][l+1]. */
+static void x_row(const cplx *n2_m, int Nz, double s, int l, cplx *lo, cplx *mid, cplx *hi)
+{
+    *lo = (l > 0) ? s : 0.0;
+    *hi = (l + 1 < Nz) ? s : 0.0;
+    *mid = (n2_m[l] - 1.0) - 2.0 * s;
+}
+
+/* u[m'][l] for the azimuth neighbour m' = m + dm (walled ghost: zero). */
+static cplx theta_nb(const cplx *u, int Nz, int Nt, int periodic, int m, int dm, int l)
+{
+    int mm = m + dm;
+    if (periodic) {
+        mm = ((mm % Nt) + Nt) % Nt;
+    } else if (mm < 0 || mm >= Nt) {
+        return 0.0;
+    }
+    return u[(size_t)mm * Nz + l];
+}
+
+/* One range step r_j -> r_j + dr, all operators evaluated at r* (Eq. 4-8).
+ * u: [Nt][Nz] in/out.  n2: [Nt][Nz] slice active at r*.                   */
+int oracle_step(int Nz, int Nt, double dz, double dtheta, double dr, double k0,
+                double rstar, int periodic, const cplx *n2, cplx *u, int nthreads)
+{
+    if (Nz <= 0 || Nt <= 0 || !(k0 > 0.0) || !(dz > 0.0) || !(dtheta > 0.0) || rstar <= 0.0)
+        return OR_ERR_ARG;
+    const cplx delta = I * (k0 * dr);
+    const double s = 1.0 / ((k0 * dz) * (k0 * dz));
+    const double c = 1.0 / ((k0 * rstar * dtheta) * (k0 * rstar * dtheta));
+    const cplx alpha = 0.25 - delta / 4.0;   /* LHS factor of X: 1/4 - d/4 */
+    const cplx beta = 0.25 + delta / 4.0;    /* RHS factor of X: 1/4 + d/4 */
+    const cplx yfac = delta / 4.0;           /* factor of Y: d/4           */
+    size_t npts = (size_t)Nz * Nt;
+    cplx *w = (cplx *)malloc(sizeof(cplx) * npts);
+    cplx *v = (cplx *)malloc(sizeof(cplx) * npts);
+    if (!w || !v) { free(w); free(v); return OR_ERR_OOM; }
+    int status = OR_OK;
+#ifdef _OPENMP
+    if (nthreads < 1) nthreads = 1;
+#endif
+    (void)nthreads;
+
+    /* 1. w = [1 + (d/4) Y] u */
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+    for (int m = 0; m < Nt; ++m)
+        for (int l = 0; l < Nz; ++l) {
+            cplx yu = c * (theta_nb(u, Nz, Nt, periodic, m, +1, l)
+                           - 2.0 * u[(size_t)m * Nz + l]
+                           + theta_nb(u, Nz, Nt, periodic, m, -1, l));
+            w[(size_t)m * Nz + l] = u[(size_t)m * Nz + l] + yfac * yu;
+        }
+
+    /* 2-3. per azimuth: RHS = [1 + beta X] w, then solve [1 + alpha X] v = RHS */
+#pragma omp parallel num_threads(nthreads)
+    {
+        cplx *sub = (cplx *)malloc(sizeof(cplx) * 7 * (size_t)Nz);
+        if (!sub) {
+#pragma omp atomic write
+            status = OR_ERR_OOM;
+        } else {
+            cplx *dg = sub + Nz, *sp = sub + 2 * Nz, *rhs = sub + 3 * Nz;
+            cplx *wd = sub + 4 * Nz, *wu1 = sub + 5 * Nz, *wu2 = sub + 6 * Nz;
+#pragma omp for schedule(static)
+            for (int m = 0; m < Nt; ++m) {
+                const cplx *n2m = n2 + (size_t)m * Nz;
+                const cplx *wm = w + (size_t)m * Nz;
+                for (int l = 0; l < Nz; ++l) {
+                    cplx lo, mid, hi;
+                    x_row(n2m, Nz, s, l, &lo, &mid, &hi);
+                    cplx xw = mid * wm[l];
+                    if (l > 0) xw = xw + lo * wm[l - 1];
+                    if (l + 1 < Nz) xw = xw + hi * wm[l + 1];
+                    rhs[l] = wm[l] + beta * xw;
+                    sub[l] = alpha * lo;
+                    dg[l] = 1.0 + alpha * mid;
+                    sp[l] = alpha * hi;
+                }
+                int rc = tridiag_gepp(Nz, sub, dg, sp, rhs, wd, wu1, wu2);
+                if (rc) {
+#pragma omp atomic write
+                    status = rc;
+                }
+                memcpy(v + (size_t)m * Nz, rhs, sizeof(cplx) * Nz);
+            }
+            free(sub);
+        }
+    }
+
+    /* 4. per depth: solve [1 - (d/4) Y] u' = v */
+    if (status == OR_OK) {
+#pragma omp parallel num_threads(nthreads)
+        {
+            cplx *sub = (cplx *)malloc(sizeof(cplx) * 10 * (size_t)Nt);
+            if (!sub) {
+#pragma omp atomic write
+                status = OR_ERR_OOM;
+            } else {
+                cplx *dg = sub + Nt, *sp = sub + 2 * Nt, *x = sub + 3 * Nt, *work = sub + 4 * Nt;
+                /* Y's row: c at m-1, -2c at m, c at m+1 (ghost-free in the periodic case) */
+                for (int m = 0; m < Nt; ++m) {
+                    cplx lo = (periodic || m > 0) ? c : 0.0;
+                    cplx hi = (periodic || m + 1 < Nt) ? c : 0.0;
+                    sub[m] = 0.0 - yfac * lo;
+                    dg[m] = 1.0 - yfac * (-2.0 * c);
+                    sp[m] = 0.0 - yfac * hi;
+                }
+#pragma omp for schedule(static)
+                for (int l = 0; l < Nz; ++l) {
+                    for (int m = 0; m < Nt; ++m) x[m] = v[(size_t)m * Nz + l];
+                    int rc = periodic ? cyclic_sm(Nt, sub, dg, sp, x, work)
+                                      : tridiag_gepp(Nt, sub, dg, sp, x, work, work + Nt, work + 2 * Nt);
+                    if (rc) {
+#pragma omp atomic write
+                        status = rc;
+                    }
+                    for (int m = 0; m < Nt; ++m) u[(size_t)m * Nz + l] = x[m];
+                }
+                free(sub);
+            }
+        }
+    }
+    free(w);
+    free(v);
+    return status;
+}
+
+/* Index of the medium slice active at range r: the last k with R_k <= r,
+ * or 0 when r precedes every slice.                                       */
+static int active_slice(const double *slice_r, int K, double r)
+{
+    int k = 0;
+    for (int i = 0; i < K; ++i)
+        if (slice_r[i] <= r) k = i;
+    return k;
+}
+
+/* The range loop of Fig. 2: steps j = 0 .. steps-1 advance r* = r0 + (j+1) dr;
+ * after step j, when (j+1) is a multiple of `stride`, the field is stored as
+ * out[(j+1)/stride - 1].  n2: [K][Nt][Nz]; u0, out snapshots: [Nt][Nz].     */
+int oracle_march(int Nz, int Nt, double dz, double dtheta, double dr, double k0, int periodic,
+                 const cplx *n2, const double *slice_r, int K, const cplx *u0, double r0,
+                 int steps, int stride, cplx *out, int nthreads)
+{
+    if (Nz <= 0 || Nt <= 0 || K <= 0 || steps < 0 || stride <= 0 || r0 <= 0.0) return OR_ERR_ARG;
+    size_t npts = (size_t)Nz * Nt;
+    cplx *u = (cplx *)malloc(sizeof(cplx) * npts);
+    if (!u) return OR_ERR_OOM;
+    memcpy(u, u0, sizeof(cplx) * npts);
+    int rc = OR_OK;
+    for (int j = 0; j < steps && rc == OR_OK; ++j) {
+        double rstar = r0 + (double)(j + 1) * dr;
+        int k = active_slice(slice_r, K, rstar);
+        rc = oracle_step(Nz, Nt, dz, dtheta, dr, k0, rstar, periodic, n2 + (size_t)k * npts, u, nthreads);
+        if (rc == OR_OK && (j + 1) % stride == 0)
+            memcpy(out + (size_t)((j + 1) / stride - 1) * npts, u, sizeof(cplx) * npts);
+    }
+    free(u);
+    return rc;
+}
