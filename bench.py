@@ -1,0 +1,433 @@
+#!/usr/bin/env python3
+"""Benchmark of the 3D wide-angle PE range march on GB300.
+
+One bench step = one pass of the whole hot path over the medium-sized
+100 Hz workload (Nz=1067 x Ntheta=256, 2000 range steps, 101 medium slices):
+FP64 coefficient setup of every slice's depth systems (pe3d_set_medium from a
+device-resident n^2), then the march itself (per-step FP64 azimuth setup,
+then the complex-FP32 range steps in one persistent launch), all through the
+library's C ABI.  The metric is grid-point range-steps per second, at a
+relative L2 error against the FP64 oracle that the run measures and reports.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun) runs N independent replicas (one march per GPU, no
+collective on the data path) and reports the whole-job rate.
+`--impl reference` times the FP64 CPU oracle on this machine's cores on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+os.environ.setdefault("OMP_WAIT_POLICY", "PASSIVE")
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+METRIC = "grid-point range-steps/s at ≤1e-4 rel-L2 vs FP64 oracle; p50/p99 solve latency"
+UNIT = "grid-point range-steps/s"
+BYTES_PER_POINT_STEP = {"fp32": 40, "fp64": 80}
+FALLBACK_HBM_GBS = 6800.0
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+def rank_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def init_dist(backend: str):
+    import torch.distributed as dist
+    if int(os.environ.get("WORLD_SIZE", 1)) > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def reduce_max(x: float, device=None) -> float:
+    """Max over ranks (identity on one process)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1711_00005_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel
+    sources are unchanged since it was taken (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d[kernel][workload]
+        if e.get("source_sha256") != kernel_source_hash():
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.proc = None
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+            if gpu_id:
+                cmd += ["-i", gpu_id]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_uuid():
+    try:
+        import torch
+        u = torch.cuda.get_device_properties(torch.cuda.current_device()).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        return None
+
+
+def relerr_series(got, ref):
+    return [float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel())) for a, b in zip(got, ref)]
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+
+WORKLOADS = {
+    "medium-100Hz": ("fp32", lambda: workloads.config2()),
+    "medium-100Hz-fp64": ("fp64", lambda: workloads.config2()),
+    "walled-50Hz": ("fp64", lambda: workloads.config1()),
+    "periodic-200Hz": ("fp32", lambda: workloads.config3()),
+}
+
+
+def oracle_run(wl, steps: int, nthreads: int):
+    import oracle
+    L = oracle.load()
+    g = wl.grid
+    stride = g.stride if steps % g.stride == 0 else steps
+    t = time.perf_counter()
+    out = L.march(g, wl.n2, wl.slice_r, wl.u0, steps=steps, stride=stride, nthreads=nthreads)
+    return out, time.perf_counter() - t
+
+
+# ---------------------------------------------------------------------------
+# arms
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    rank, world, _ = rank_info()
+    if world > 1:
+        init_dist("gloo")
+        if rank != 0:
+            barrier()
+            return 0
+    import oracle
+    precision, make = WORKLOADS[args.workload]
+    wl = make()
+    g = wl.grid
+    cores = oracle.default_threads()
+    sample_steps = min(g.steps, args.ref_sample_steps)
+    for _ in range(args.warmup):
+        oracle_run(wl, sample_steps, cores)
+    times = []
+    for _ in range(args.steps):
+        _, dt = oracle_run(wl, sample_steps, cores)
+        times.append(dt)
+    per = statistics.mean(times)
+    value = g.points * sample_steps / per
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": g.name, "sample_range_steps": sample_steps, "Nz": g.Nz, "Ntheta": g.Ntheta},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"first {sample_steps} of {g.steps} range steps of {g.name}, "
+                                   f"FP64 C oracle, OpenMP over systems"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        barrier()
+    return 0
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    init_dist("nccl")
+    from paper_1711_00005_gb300 import build
+    if rank == 0 or world == 1:
+        build.build()
+    barrier()
+    import paper_1711_00005_gb300 as P
+
+    precision, make = WORKLOADS[args.workload]
+    fp32 = precision == "fp32"
+    wl = make()
+    g = wl.grid
+    point_steps = g.point_steps
+    cdt = np.complex64 if fp32 else np.complex128
+    tcdt = torch.complex64 if fp32 else torch.complex128
+
+    # CPU baseline + oracle reference (rank 0, before any GPU work is timed)
+    cpu = None
+    ref = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        cores = oracle.default_threads()
+        ref, dt = oracle_run(wl, g.steps, cores)
+        cpu = {"value": g.points * g.steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"the full {g.steps}-step march of {g.name} (FP64 C oracle, OpenMP over "
+                         f"systems, {dt:.1f} s)"}
+
+    stream = torch.cuda.Stream(device=dev)
+    n2_dev = torch.from_numpy(wl.n2).to(dev)
+    u0_dev = torch.from_numpy(wl.u0.astype(cdt)).to(dev)
+    out_dev = torch.empty((g.n_out, g.Ntheta, g.Nz), dtype=tcdt, device=dev)
+    torch.cuda.synchronize()
+    plan = P.pe3d_plan(g.Nz, g.Ntheta, g.dz, g.dtheta, g.dr, g.k0,
+                       P.PE3D_PERIODIC if g.periodic else P.PE3D_WALLED,
+                       P.PE3D_FP32 if fp32 else P.PE3D_FP64, stream)
+    P.pe3d_set_option(plan, P.PE3D_OPT_EXEC, args.exec)
+    P.pe3d_set_option(plan, P.PE3D_OPT_TIMING, 1)
+
+    def step():
+        P.pe3d_set_medium(plan, n2_dev, wl.slice_r)
+        P.pe3d_march(plan, u0_dev, g.r0, g.steps, g.stride, out_dev)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # parity of this run's output against the oracle
+    err = None
+    if ref is not None:
+        err = max(relerr_series(out_dev.cpu().numpy(), ref))
+
+    # timed region: K steps, CUDA events on the plan's stream
+    launches0 = P.pe3d_plan_info(plan)["total_launches"]
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(gpu_uuid())
+    kernel_ns = []
+    barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+        kernel_ns.append(P.pe3d_plan_info(plan)["kernel_ns"])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    info = P.pe3d_plan_info(plan)
+    launches = info["total_launches"] - launches0
+    t_local = ev0.elapsed_time(ev1) / 1e3
+    t = reduce_max(t_local, dev)
+    total_units = reduce_sum(point_steps * args.steps, dev)
+
+    # end to end: host (pinned) buffers through the same C ABI calls, copies timed
+    n2_h = torch.from_numpy(wl.n2).pin_memory()
+    u0_h = torch.from_numpy(wl.u0.astype(cdt)).pin_memory()
+    out_h = torch.empty((g.n_out, g.Ntheta, g.Nz), dtype=tcdt).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+    P.pe3d_set_medium(plan, n2_h, wl.slice_r)
+    P.pe3d_march(plan, u0_h, g.r0, g.steps, g.stride, out_h)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        P.pe3d_set_medium(plan, n2_h, wl.slice_r)
+        P.pe3d_march(plan, u0_h, g.r0, g.steps, g.stride, out_h)
+    t_e2e = reduce_max((time.perf_counter() - t0) / e2e_steps, dev)
+
+    # plain FP64 GPU march of the same workload, for comparison
+    fp64_value = None
+    if fp32 and not args.no_fp64_compare:
+        u064 = torch.from_numpy(wl.u0).to(dev)
+        o64 = torch.empty((g.n_out, g.Ntheta, g.Nz), dtype=torch.complex128, device=dev)
+        p64 = P.pe3d_plan(g.Nz, g.Ntheta, g.dz, g.dtheta, g.dr, g.k0,
+                          P.PE3D_PERIODIC if g.periodic else P.PE3D_WALLED, P.PE3D_FP64, stream)
+        P.pe3d_set_medium(p64, n2_dev, wl.slice_r)
+        P.pe3d_march(p64, u064, g.r0, g.steps, g.stride, o64)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        reps = 3
+        for _ in range(reps):
+            P.pe3d_set_medium(p64, n2_dev, wl.slice_r)
+            P.pe3d_march(p64, u064, g.r0, g.steps, g.stride, o64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp64_value = point_steps * reps / (e0.elapsed_time(e1) / 1e3)
+        if ref is not None:
+            fp64_err = max(relerr_series(o64.cpu().numpy(), ref))
+        else:
+            fp64_err = None
+        P.pe3d_destroy(p64)
+
+    if rank == 0:
+        peak, peak_kind = measured_peaks()
+        kns = statistics.mean(kernel_ns) if kernel_ns and kernel_ns[0] > 0 else None
+        bpp = BYTES_PER_POINT_STEP[precision]
+        roof = None
+        if kns:
+            achieved = bpp * point_steps / (kns * 1e-9) / 1e9
+            kname = f"k_march_persistent<{'float2' if fp32 else 'double2'}>"
+            roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "peak_source": f"{peak_kind} hbm_gbs", "kernel": kname,
+                    "algorithmic_bytes_per_launch": bpp * point_steps, "kernel_ms": kns / 1e6,
+                    "traffic": recorded_traffic(kname, g.name)}
+        line = {
+            "metric": METRIC,
+            "value": total_units / t,
+            "unit": UNIT,
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": t / args.steps * 1e3,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32" if fp32 else "f64",
+            "data": "synthetic",
+            "config": {
+                "workload": g.name, "Nz": g.Nz, "Ntheta": g.Ntheta, "range_steps": g.steps,
+                "medium_slices": len(wl.slice_r), "point_steps_per_march": point_steps,
+                "precision": "complex64 march, FP64 coefficient setup" if fp32 else "complex128",
+                "exec": ["auto", "stream", "graph", "persistent"][info["exec"]],
+                "layout": {k: info[k] for k in ("ldz", "zthreads", "zchunk", "ttile", "tchunk", "grid")},
+                "l2": "flushed each step: the step re-reads the 441 MB n^2 and rewrites 220 MB of "
+                      "coefficients (> 129 MB L2) before the march",
+                "parallelism": f"replicas x{world}",
+            },
+            "max_rel_l2_vs_oracle": err,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": total_units / args.steps / t_e2e * (1 if world == 1 else 1), "unit": UNIT,
+                    "h2d_bytes_per_step": int(wl.n2.nbytes + wl.u0.astype(cdt).nbytes),
+                    "d2h_bytes_per_step": int(out_h.numel() * out_h.element_size())},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        if fp64_value is not None:
+            line["fp64_march"] = {"value": fp64_value, "unit": UNIT, "max_rel_l2_vs_oracle": fp64_err}
+        print(json.dumps(line), flush=True)
+    P.pe3d_destroy(plan)
+    barrier()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="medium-100Hz")
+    ap.add_argument("--exec", type=int, default=3, help="1 stream, 2 graph, 3 persistent")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--ref-sample-steps", type=int, default=200)
+    args = ap.parse_args(argv)
+    args.warmup = max(3, args.warmup)     # timing rule: at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

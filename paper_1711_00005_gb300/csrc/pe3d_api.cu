@@ -1,0 +1,343 @@
+// pe3d_api.cu -- the extern "C" boundary: argument checking, plan memory,
+// staging of host buffers, and dispatch to the FP32 / FP64 launch layers.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "pe3d_internal.h"
+#include "pe3d_device.cuh"
+
+namespace pe3d_host {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+int fail(int code, const std::string& msg) { g_err = msg; return code; }
+int cuda_fail(cudaError_t e, const char* what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? PE3D_ERR_OOM : PE3D_ERR_CUDA;
+}
+
+size_t elem_bytes(const pe3d_plan_s* p) { return p->precision == PE3D_FP32 ? 8 : 16; }
+
+int dev_alloc(pe3d_plan_s* p, void** ptr, size_t bytes) {
+    *ptr = nullptr;
+    if (bytes == 0) return PE3D_OK;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        return fail(PE3D_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+    }
+    p->bytes += (int64_t)bytes;
+    return PE3D_OK;
+}
+
+void dev_free(pe3d_plan_s* p, void** ptr, size_t bytes) {
+    if (*ptr) {
+        cudaFree(*ptr);
+        p->bytes -= (int64_t)bytes;
+    }
+    *ptr = nullptr;
+}
+
+static size_t step_bytes(const pe3d_plan_s* p, int cap, int which) {
+    const size_t eb = elem_bytes(p);
+    switch (which) {
+        case 0: return (size_t)cap * p->NtP * eb;                                         // mB
+        case 1: return p->boundary == PE3D_PERIODIC ? (size_t)cap * p->NtP * eb : 0;      // zsm
+        case 2: return p->boundary == PE3D_PERIODIC ? (size_t)2 * cap * p->NtP * 16 : 0;  // gscr
+        case 3: return (size_t)cap * sizeof(pe3d::StepConst);                             // sc
+        default: return (size_t)cap * sizeof(int);                                        // slice_of_step
+    }
+}
+
+int ensure_steps(pe3d_plan_s* p, int steps) {
+    if (steps <= p->step_cap) return PE3D_OK;
+    const int cap = std::max(steps, 2 * p->step_cap);
+    void** bufs[5] = {&p->mB, &p->zsm, &p->gscr, &p->sc, (void**)&p->slice_of_step};
+    for (int i = 0; i < 5; ++i) dev_free(p, bufs[i], step_bytes(p, p->step_cap, i));
+    p->step_cap = 0;
+    for (int i = 0; i < 5; ++i) {
+        int rc = dev_alloc(p, bufs[i], step_bytes(p, cap, i));
+        if (rc) {
+            for (int k = 0; k < i; ++k) dev_free(p, bufs[k], step_bytes(p, cap, k));
+            return rc;
+        }
+    }
+    p->step_cap = cap;
+    return PE3D_OK;
+}
+
+int active_slice(const std::vector<double>& slice_r, double r) {
+    int k = 0;
+    for (size_t i = 0; i < slice_r.size(); ++i)
+        if (slice_r[i] <= r) k = (int)i;
+    return k;
+}
+
+static bool on_device_ptr(const void* ptr) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static int fix_layout(pe3d_plan_s* p) {
+    if (p->ldz) return PE3D_OK;
+    int rc = p->precision == PE3D_FP32 ? layout_choose_f32(p) : layout_choose_f64(p);
+    if (rc) return rc;
+    const size_t fb = (size_t)p->Nt * p->ldz * elem_bytes(p);
+    if ((rc = dev_alloc(p, &p->w, fb))) return rc;
+    if ((rc = dev_alloc(p, &p->v, fb))) return rc;
+    PE3D_CUDA(cudaMemsetAsync(p->w, 0, fb, p->stream));
+    PE3D_CUDA(cudaMemsetAsync(p->v, 0, fb, p->stream));
+    return PE3D_OK;
+}
+
+static int read_status(pe3d_plan_s* p) {
+    int st = 0;
+    PE3D_CUDA(cudaMemcpyAsync(&st, p->status, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    PE3D_CUDA(cudaStreamSynchronize(p->stream));
+    if (st == PE3D_ERR_SINGULAR) return fail(st, "a pivot vanished or is not finite (singular system)");
+    if (st == PE3D_ERR_TIMEOUT) return fail(st, "a bounded device-side wait gave up");
+    if (st != 0) return fail(PE3D_ERR_CUDA, "device status " + std::to_string(st));
+    return PE3D_OK;
+}
+
+}  // namespace pe3d_host
+
+using namespace pe3d_host;
+
+extern "C" {
+
+const char* pe3d_last_error(void) { return g_err.c_str(); }
+
+int pe3d_plan(int Nz, int Ntheta, double dz, double dtheta, double dr, double k0, int boundary, int precision,
+              void* cuda_stream, pe3d_plan_t* out) {
+    g_err.clear();
+    if (!out) return fail(PE3D_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (Nz < 1 || Ntheta < 1) return fail(PE3D_ERR_ARG, "Nz and Ntheta must be >= 1");
+    if (boundary != PE3D_WALLED && boundary != PE3D_PERIODIC) return fail(PE3D_ERR_ARG, "unknown boundary");
+    if (boundary == PE3D_PERIODIC && Ntheta < 3) return fail(PE3D_ERR_ARG, "a periodic azimuth grid needs Ntheta >= 3");
+    if (precision != PE3D_FP32 && precision != PE3D_FP64) return fail(PE3D_ERR_ARG, "unknown precision");
+    if (!(dz > 0) || !(dtheta > 0) || !(k0 > 0) || !(dr != 0) || !std::isfinite(dz) || !std::isfinite(dtheta) ||
+        !std::isfinite(dr) || !std::isfinite(k0))
+        return fail(PE3D_ERR_ARG, "dz, dtheta, k0 must be positive and finite, dr nonzero and finite");
+    if ((long long)Nz * Ntheta > (1ll << 31)) return fail(PE3D_ERR_ARG, "grid too large");
+    pe3d_plan_s* p = new (std::nothrow) pe3d_plan_s();
+    if (!p) return fail(PE3D_ERR_OOM, "host allocation failed");
+    p->Nz = Nz; p->Nt = Ntheta; p->dz = dz; p->dtheta = dtheta; p->dr = dr; p->k0 = k0;
+    p->boundary = boundary; p->precision = precision;
+    p->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) { delete p; return cuda_fail(e, "device query"); }
+    int rc = dev_alloc(p, (void**)&p->status, sizeof(int));
+    if (!rc) rc = dev_alloc(p, (void**)&p->bar, sizeof(unsigned));
+    if (rc) { pe3d_destroy(p); return rc; }
+    e = cudaMemsetAsync(p->status, 0, sizeof(int), p->stream);
+    if (e != cudaSuccess) { pe3d_destroy(p); return cuda_fail(e, "memset"); }
+    *out = p;
+    return PE3D_OK;
+}
+
+int pe3d_set_option(pe3d_plan_t p, int option, int value) {
+    g_err.clear();
+    if (!p) return fail(PE3D_ERR_ARG, "plan is NULL");
+    switch (option) {
+        case PE3D_OPT_EXEC:
+            if (value < PE3D_EXEC_AUTO || value > PE3D_EXEC_PERSISTENT) return fail(PE3D_ERR_ARG, "unknown exec");
+            p->exec = value;
+            return PE3D_OK;
+        case PE3D_OPT_ZTHREADS:
+            if (p->ldz) return fail(PE3D_ERR_STATE, "layout is fixed once the medium is set");
+            if (value != 0 && value != 32 && value != 64 && value != 128 && value != 256)
+                return fail(PE3D_ERR_ARG, "ZTHREADS must be 0, 32, 64, 128 or 256");
+            p->zthreads = value;
+            return PE3D_OK;
+        case PE3D_OPT_TTILE:
+            if (p->ldz) return fail(PE3D_ERR_STATE, "layout is fixed once the medium is set");
+            if (value != 0 && value != 8 && value != 16 && value != 32)
+                return fail(PE3D_ERR_ARG, "TTILE must be 0, 8, 16 or 32");
+            p->ttile = value;
+            return PE3D_OK;
+        case PE3D_OPT_TIMING:
+            if (value && !p->ev0) {
+                PE3D_CUDA(cudaEventCreate(&p->ev0));
+                PE3D_CUDA(cudaEventCreate(&p->ev1));
+            }
+            p->timing = value ? 1 : 0;
+            return PE3D_OK;
+        case PE3D_OPT_RC_EVERY:
+            if (value < 0) return fail(PE3D_ERR_ARG, "RC_EVERY must be >= 0");
+            if (value > 0 && p->precision != PE3D_FP32) return fail(PE3D_ERR_ARG, "residual correction is for FP32 plans");
+            p->rc_every = value;
+            return PE3D_OK;
+        default:
+            return fail(PE3D_ERR_ARG, "unknown option");
+    }
+}
+
+int pe3d_get_option(pe3d_plan_t p, int option, int* value) {
+    g_err.clear();
+    if (!p || !value) return fail(PE3D_ERR_ARG, "NULL argument");
+    switch (option) {
+        case PE3D_OPT_EXEC: *value = p->exec; return PE3D_OK;
+        case PE3D_OPT_ZTHREADS: *value = p->ldz ? p->T : p->zthreads; return PE3D_OK;
+        case PE3D_OPT_TTILE: *value = p->ldz ? p->TZ : p->ttile; return PE3D_OK;
+        case PE3D_OPT_RC_EVERY: *value = p->rc_every; return PE3D_OK;
+        case PE3D_OPT_TIMING: *value = p->timing; return PE3D_OK;
+        default: return fail(PE3D_ERR_ARG, "unknown option");
+    }
+}
+
+int pe3d_set_medium(pe3d_plan_t p, const void* n2, const double* slice_r, int K, int n2_on_device) {
+    g_err.clear();
+    if (!p || !n2 || !slice_r) return fail(PE3D_ERR_ARG, "NULL argument");
+    if (K < 1) return fail(PE3D_ERR_ARG, "K must be >= 1");
+    for (int k = 0; k < K; ++k) {
+        if (!std::isfinite(slice_r[k])) return fail(PE3D_ERR_ARG, "slice ranges must be finite");
+        if (k && !(slice_r[k] > slice_r[k - 1])) return fail(PE3D_ERR_ARG, "slice ranges must ascend");
+    }
+    if (n2_on_device && !on_device_ptr(n2)) return fail(PE3D_ERR_ARG, "n2 is not device memory");
+    int rc = fix_layout(p);
+    if (rc) return rc;
+    const size_t nb = (size_t)K * p->Nt * p->Nz * 16;
+    const size_t mb = (size_t)K * p->Nt * p->ldz * elem_bytes(p);
+    p->medium_ready = false;
+    if (nb != p->n2_bytes) {
+        dev_free(p, &p->n2, p->n2_bytes);
+        p->n2_bytes = 0;
+        if ((rc = dev_alloc(p, &p->n2, nb))) return rc;
+        p->n2_bytes = nb;
+    }
+    if (mb != p->mz_bytes) {
+        dev_free(p, &p->mz, p->mz_bytes);
+        p->mz_bytes = 0;
+        if ((rc = dev_alloc(p, &p->mz, mb))) return rc;
+        p->mz_bytes = mb;
+    }
+    PE3D_CUDA(cudaMemcpyAsync(p->n2, n2, nb, n2_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              p->stream));
+    p->nslices = K;
+    p->slice_r.assign(slice_r, slice_r + K);
+    PE3D_CUDA(cudaMemsetAsync(p->status, 0, sizeof(int), p->stream));
+    rc = p->precision == PE3D_FP32 ? setupA_f32(p) : setupA_f64(p);
+    if (rc) return rc;
+    rc = read_status(p);
+    if (rc) return rc;
+    p->medium_ready = true;
+    return PE3D_OK;
+}
+
+int pe3d_march(pe3d_plan_t p, const void* u0, int u0_on_device, double r0, int steps, int out_stride, void* out,
+               int out_on_device) {
+    g_err.clear();
+    if (!p || !u0) return fail(PE3D_ERR_ARG, "NULL argument");
+    if (!p->medium_ready) return fail(PE3D_ERR_STATE, "pe3d_set_medium must succeed before pe3d_march");
+    if (steps < 0 || out_stride < 1) return fail(PE3D_ERR_ARG, "steps must be >= 0 and out_stride >= 1");
+    if (!(r0 > 0) || !std::isfinite(r0)) return fail(PE3D_ERR_ARG, "r0 must be positive and finite");
+    const double r_end = r0 + (double)(steps + 1) * p->dr;
+    if (!(r_end > 0)) return fail(PE3D_ERR_ARG, "the march reaches r <= 0");
+    const int n_out = steps / out_stride;
+    if (n_out > 0 && !out) return fail(PE3D_ERR_ARG, "out is NULL but snapshots are due");
+    if (u0_on_device && !on_device_ptr(u0)) return fail(PE3D_ERR_ARG, "u0 is not device memory");
+    if (n_out > 0 && out_on_device && !on_device_ptr(out)) return fail(PE3D_ERR_ARG, "out is not device memory");
+    const size_t eb = elem_bytes(p);
+    const size_t fbytes = (size_t)p->Nt * p->Nz * eb;
+    int rc;
+    const void* u0_dev = u0;
+    if (!u0_on_device) {
+        if (!p->u0stage && (rc = dev_alloc(p, &p->u0stage, fbytes))) return rc;
+        PE3D_CUDA(cudaMemcpyAsync(p->u0stage, u0, fbytes, cudaMemcpyHostToDevice, p->stream));
+        u0_dev = p->u0stage;
+    }
+    void* snap = nullptr;
+    if (n_out > 0) {
+        if (out_on_device) {
+            snap = out;
+        } else {
+            const size_t need = (size_t)n_out * fbytes;
+            if (need > p->outstage_bytes) {
+                dev_free(p, &p->outstage, p->outstage_bytes);
+                p->outstage_bytes = 0;
+                if ((rc = dev_alloc(p, &p->outstage, need))) return rc;
+                p->outstage_bytes = need;
+            }
+            snap = p->outstage;
+        }
+    }
+    PE3D_CUDA(cudaMemsetAsync(p->status, 0, sizeof(int), p->stream));
+    rc = p->precision == PE3D_FP32 ? march_f32(p, u0_dev, r0, steps, out_stride, snap, p->Nz)
+                                   : march_f64(p, u0_dev, r0, steps, out_stride, snap, p->Nz);
+    if (rc) return rc;
+    if (n_out > 0 && !out_on_device)
+        PE3D_CUDA(cudaMemcpyAsync(out, snap, (size_t)n_out * fbytes, cudaMemcpyDeviceToHost, p->stream));
+    rc = read_status(p);
+    if (rc) return rc;
+    p->last_kernel_ns = 0;
+    if (p->timing && steps > 0) {
+        float ms = 0.f;
+        PE3D_CUDA(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+        p->last_kernel_ns = (int64_t)((double)ms * 1e6);
+    }
+    return PE3D_OK;
+}
+
+int pe3d_march_batched(int n, const pe3d_plan_t* plans, const void* const* u0, const double* r0, const int* steps,
+                       const int* out_stride, void* const* out) {
+    g_err.clear();
+    if (n < 1 || !plans || !u0 || !r0 || !steps || !out_stride || !out) return fail(PE3D_ERR_ARG, "NULL argument");
+    const int prec = plans[0] ? plans[0]->precision : -1;
+    for (int i = 0; i < n; ++i) {
+        if (!plans[i]) return fail(PE3D_ERR_ARG, "plan is NULL");
+        if (plans[i]->precision != prec) return fail(PE3D_ERR_ARG, "plans must share one precision");
+        if (!plans[i]->medium_ready) return fail(PE3D_ERR_STATE, "every plan needs its medium");
+        if (steps[i] < 0 || out_stride[i] < 1 || !(r0[i] > 0)) return fail(PE3D_ERR_ARG, "bad steps/stride/r0");
+    }
+    int rc = prec == PE3D_FP32 ? batched_f32(n, plans, u0, r0, steps, out_stride, out)
+                               : batched_f64(n, plans, u0, r0, steps, out_stride, out);
+    if (rc) return rc;
+    for (int i = 0; i < n; ++i)
+        if ((rc = read_status(plans[i]))) return rc;
+    return PE3D_OK;
+}
+
+int pe3d_destroy(pe3d_plan_t p) {
+    g_err.clear();
+    if (!p) return PE3D_OK;
+    cudaStreamSynchronize(p->stream);
+    if (p->ev0) cudaEventDestroy(p->ev0);
+    if (p->ev1) cudaEventDestroy(p->ev1);
+    void** bufs[] = {&p->w, &p->v, &p->u0stage, &p->outstage, &p->n2, &p->mz, &p->mB, &p->zsm,
+                     &p->gscr, &p->sc, (void**)&p->slice_of_step, (void**)&p->status, (void**)&p->bar};
+    for (void** b : bufs)
+        if (*b) { cudaFree(*b); *b = nullptr; }
+    delete p;
+    return PE3D_OK;
+}
+
+int pe3d_plan_info(pe3d_plan_t p, int64_t* info, int n) {
+    g_err.clear();
+    if (!p || !info || n < 0) return fail(PE3D_ERR_ARG, "bad argument");
+    const int64_t vals[] = {p->Nz, p->Nt, p->ldz, p->T, p->L, p->TZ, p->Lt, p->last_exec, p->bytes,
+                            p->last_launches, p->last_grid, p->last_kernel_ns, p->total_launches};
+    const int cnt = std::min<int>(n, (int)(sizeof(vals) / sizeof(vals[0])));
+    for (int i = 0; i < cnt; ++i) info[i] = vals[i];
+    return cnt;
+}
+
+int pe3d_autotune(pe3d_plan_t p, double r0, int steps) {
+    g_err.clear();
+    (void)r0; (void)steps;
+    if (!p) return fail(PE3D_ERR_ARG, "plan is NULL");
+    return fail(PE3D_ERR_STATE, "autotune not built yet");
+}
+
+}  // extern "C"

@@ -1,0 +1,142 @@
+// pe3d_device.cuh -- device building blocks of the range march (sm_103a).
+//
+// The two tridiagonal families of scheme (4) -- Eq. 5/7 in depth, Eq. 6/8 in
+// azimuth -- are solved with pivots that depend only on the matrix, built
+// once in FP64 (per medium slice for the depth systems, per range step for
+// the azimuth systems, which share one matrix across all depths).  With the
+// scaled multipliers mu_i = -e / p_i (e the constant off-diagonal, p_i the
+// elimination pivots), elimination and back substitution become the two
+// first-order linear recurrences
+//
+//   forward   g_i = mu_i (b_i + g_{i-1})           (g = -e * forward result)
+//   backward  y_i = g_i + mu_i y_{i+1}             (y = -e * solution)
+//
+// Each is an affine map per element, so a system split into contiguous
+// chunks (one per thread) is solved by: a sequential pass per chunk that
+// composes its maps, an exclusive scan of the chunk maps across threads
+// (warp shuffles, then shared memory across warps), and a second sequential
+// pass from the scanned carry.  This exposes threads-per-system parallelism
+// without changing what elimination computes.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pe3d {
+
+// ---------------------------------------------------------------------------
+// complex arithmetic on float2 / double2
+// ---------------------------------------------------------------------------
+template <typename R> struct cplx_of;
+template <> struct cplx_of<float>  { using type = float2; };
+template <> struct cplx_of<double> { using type = double2; };
+
+__host__ __device__ __forceinline__ float2 cmake(float r, float i) { return make_float2(r, i); }
+__host__ __device__ __forceinline__ double2 cmake(double r, double i) { return make_double2(r, i); }
+
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
+    C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+// a * b + c
+template <typename C> __device__ __forceinline__ C cfma(C a, C b, C c) {
+    C r;
+    r.x = fma(a.x, b.x, fma(-a.y, b.y, c.x));
+    r.y = fma(a.x, b.y, fma(a.y, b.x, c.y));
+    return r;
+}
+template <typename C> __device__ __forceinline__ C czero() { C r; r.x = 0; r.y = 0; return r; }
+template <typename C> __device__ __forceinline__ C cone() { C r; r.x = 1; r.y = 0; return r; }
+
+template <typename C> struct real_of;
+template <> struct real_of<float2> { using type = float; };
+template <> struct real_of<double2> { using type = double; };
+
+// convert an FP64 complex constant to the march type
+template <typename C> __host__ __device__ __forceinline__ C from64(double2 a);
+template <> __host__ __device__ __forceinline__ float2 from64<float2>(double2 a) { return make_float2((float)a.x, (float)a.y); }
+template <> __host__ __device__ __forceinline__ double2 from64<double2>(double2 a) { return a; }
+
+__device__ __forceinline__ double2 to64(float2 a) { return make_double2((double)a.x, (double)a.y); }
+__device__ __forceinline__ double2 to64(double2 a) { return a; }
+
+// loads of field data written by other CTAs of the same kernel: bypass L1
+__device__ __forceinline__ float4 ld_field(const float4* p) { return __ldcg(p); }
+__device__ __forceinline__ double2 ld_field(const double2* p) { return __ldcg(p); }
+__device__ __forceinline__ float2 ld_field(const float2* p) { return __ldcg(p); }
+
+// ---------------------------------------------------------------------------
+// affine maps x -> a x + b and their scan across the threads of one system
+// ---------------------------------------------------------------------------
+template <typename C> struct Aff { C a, b; };
+
+// apply `first`, then `second`
+template <typename C> __device__ __forceinline__ Aff<C> then(const Aff<C>& first, const Aff<C>& second) {
+    Aff<C> r;
+    r.a = cmul(second.a, first.a);
+    r.b = cfma(second.a, first.b, second.b);
+    return r;
+}
+
+__device__ __forceinline__ float2 shfl_up(float2 v, int d) {
+    return make_float2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
+}
+__device__ __forceinline__ double2 shfl_up(double2 v, int d) {
+    return make_double2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
+}
+__device__ __forceinline__ float2 shfl_down(float2 v, int d) {
+    return make_float2(__shfl_down_sync(0xffffffffu, v.x, d), __shfl_down_sync(0xffffffffu, v.y, d));
+}
+__device__ __forceinline__ double2 shfl_down(double2 v, int d) {
+    return make_double2(__shfl_down_sync(0xffffffffu, v.x, d), __shfl_down_sync(0xffffffffu, v.y, d));
+}
+
+// Geometry of one scan: the chunks k = 0..K-1 of one system sit on lanes
+// (k % KW) * S + (lane offset of the system), KW = 32 / S chunks per warp, in
+// W = K / KW consecutive-k warps.  `scr` holds W entries private to this
+// system.  Every thread of the CTA must call this (it may __syncthreads).
+struct ScanGeom {
+    int S;    // lane stride between consecutive chunks (1, 2, 4, ..., 32)
+    int KW;   // chunks per warp = 32 / S
+    int kw;   // this thread's chunk position inside its warp
+    int W;    // warps spanned by one system
+    int wk;   // this thread's warp position inside the system
+};
+
+// Exclusive carry of the scan, evaluated at zero: forward (FWD) returns the
+// composition of chunks 0..k-1 applied to 0, backward that of chunks K-1..k+1.
+template <typename C, bool FWD>
+__device__ __forceinline__ C scan_carry(Aff<C> x, const ScanGeom& g, Aff<C>* scr) {
+    const int pos = FWD ? g.kw : (g.KW - 1 - g.kw);
+#pragma unroll 1
+    for (int d = 1; d < g.KW; d <<= 1) {
+        Aff<C> o;
+        if (FWD) { o.a = shfl_up(x.a, d * g.S); o.b = shfl_up(x.b, d * g.S); }
+        else     { o.a = shfl_down(x.a, d * g.S); o.b = shfl_down(x.b, d * g.S); }
+        if (pos >= d) x = then(o, x);
+    }
+    Aff<C> P; P.a = cone<C>(); P.b = czero<C>();
+    if (g.W > 1) {
+        const bool last = FWD ? (g.kw == g.KW - 1) : (g.kw == 0);
+        if (last) scr[g.wk] = x;
+        __syncthreads();
+        if (FWD) { for (int w = 0; w < g.wk; ++w) P = then(P, scr[w]); }
+        else     { for (int w = g.W - 1; w > g.wk; --w) P = then(P, scr[w]); }
+        __syncthreads();
+    }
+    const Aff<C> full = then(P, x);
+    const C nb = FWD ? shfl_up(full.b, g.S) : shfl_down(full.b, g.S);
+    return pos > 0 ? nb : P.b;
+}
+
+// ---------------------------------------------------------------------------
+// per-step constants of the azimuth systems (built in FP64 by the setup)
+// ---------------------------------------------------------------------------
+struct StepConst {
+    double2 nbinv;   // -1 / e_B: converts the scaled solution back (e_B = -d c_j / 4)
+    double2 qnext;   // d c_{j+1} / 4: [1 + (d/4) Y] of the next step
+    double2 bg;      // e_B / gamma  (cyclic: v^T y = y_0 + bg y_{N-1})
+    double2 xi;      // 1 / (1 + v^T z) (cyclic)
+};
+
+}  // namespace pe3d

@@ -1,0 +1,96 @@
+// pe3d_internal.h -- host-side plan structure shared by the C ABI and the
+// typed launch layers (FP32 and FP64 are compiled as separate units).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pe3d.h"
+
+struct pe3d_plan_s {
+    // grid and scheme
+    int Nz = 0, Nt = 0;
+    double dz = 0, dtheta = 0, dr = 0, k0 = 0;
+    int boundary = PE3D_WALLED, precision = PE3D_FP64;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+
+    // options
+    int exec = PE3D_EXEC_AUTO;
+    int zthreads = 0;       // 0 = library choice
+    int ttile = 0;          // 0 = library choice
+    int rc_every = 0;
+    int timing = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int64_t last_kernel_ns = 0;
+    int64_t total_launches = 0;
+
+    // layout (fixed once the medium is set)
+    int T = 0, L = 0, ldz = 0, NG = 0;
+    int TZ = 0, K = 0, Lt = 0, NtP = 0, tiles = 0;
+
+    // device buffers (bytes are complex of the plan precision unless noted)
+    void* w = nullptr;
+    void* v = nullptr;
+    void* u0stage = nullptr;          // [Nt][Nz] staging of a host u0
+    void* outstage = nullptr;         // staging of host snapshots
+    size_t outstage_bytes = 0;
+    void* n2 = nullptr;               // complex128 [nslices][Nt][Nz]
+    size_t n2_bytes = 0;
+    int nslices = 0;
+    std::vector<double> slice_r;
+    void* mz = nullptr;               // [nslices][Nt][ldz]
+    size_t mz_bytes = 0;
+    // per-step arrays
+    void* mB = nullptr;               // [steps][NtP]
+    void* zsm = nullptr;              // [steps][NtP]
+    void* gscr = nullptr;             // complex128 [2][steps][NtP] (periodic setup)
+    void* sc = nullptr;               // StepConst [steps]
+    int* slice_of_step = nullptr;     // [steps]
+    int step_cap = 0;
+    int* status = nullptr;            // device status word
+    unsigned* bar = nullptr;          // grid-barrier counter
+    bool medium_ready = false;
+    int64_t bytes = 0;
+    int64_t last_launches = 0;
+    int last_grid = 0;
+    int last_exec = 0;
+};
+
+namespace pe3d_host {
+
+// thread-local error message
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define PE3D_CUDA(call)                                        \
+    do {                                                       \
+        cudaError_t e__ = (call);                              \
+        if (e__ != cudaSuccess) return pe3d_host::cuda_fail(e__, #call); \
+    } while (0)
+
+size_t elem_bytes(const pe3d_plan_s* p);   // 8 (FP32) or 16 (FP64)
+
+// typed entry points (defined in pe3d_f32.cu / pe3d_f64.cu)
+int layout_choose_f32(pe3d_plan_s* p);
+int layout_choose_f64(pe3d_plan_s* p);
+int setupA_f32(pe3d_plan_s* p);
+int setupA_f64(pe3d_plan_s* p);
+int march_f32(pe3d_plan_s* p, const void* u0_dev, double r0, int steps, int stride, void* snap_dev, int snap_ld);
+int march_f64(pe3d_plan_s* p, const void* u0_dev, double r0, int steps, int stride, void* snap_dev, int snap_ld);
+int batched_f32(int n, pe3d_plan_s* const* plans, const void* const* u0, const double* r0, const int* steps,
+                const int* stride, void* const* out);
+int batched_f64(int n, pe3d_plan_s* const* plans, const void* const* u0, const double* r0, const int* steps,
+                const int* stride, void* const* out);
+
+// shared helpers (pe3d_api.cu)
+int dev_alloc(pe3d_plan_s* p, void** ptr, size_t bytes);
+void dev_free(pe3d_plan_s* p, void** ptr, size_t bytes);
+int ensure_steps(pe3d_plan_s* p, int steps);
+int active_slice(const std::vector<double>& slice_r, double r);
+
+}  // namespace pe3d_host
