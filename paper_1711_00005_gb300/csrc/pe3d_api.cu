@@ -87,6 +87,33 @@ static bool on_device_ptr(const void* ptr) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// The azimuth tile of v as a 2-D tensor for TMA: x = depth in 8-byte units
+// (a complex64 is one unit, a complex128 two), y = azimuth; box TZ x BY.
+int encode_tmap_v(pe3d_plan_s* p) {
+    using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static EncodeFn encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            return fail(PE3D_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+        encode = reinterpret_cast<EncodeFn>(fn);
+    }
+    const cuuint64_t units = elem_bytes(p) / 8;
+    const cuuint64_t dims[2] = {(cuuint64_t)p->ldz * units, (cuuint64_t)p->Nt};
+    const cuuint64_t strides[1] = {(cuuint64_t)p->ldz * elem_bytes(p)};
+    const cuuint32_t box[2] = {(cuuint32_t)(p->TZ * units), (cuuint32_t)p->BY};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(&p->tmap_v, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, p->v, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(PE3D_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return PE3D_OK;
+}
+
 static int fix_layout(pe3d_plan_s* p) {
     if (p->ldz) return PE3D_OK;
     int rc = p->precision == PE3D_FP32 ? layout_choose_f32(p) : layout_choose_f64(p);
@@ -96,7 +123,7 @@ static int fix_layout(pe3d_plan_s* p) {
     if ((rc = dev_alloc(p, &p->v, fb))) return rc;
     PE3D_CUDA(cudaMemsetAsync(p->w, 0, fb, p->stream));
     PE3D_CUDA(cudaMemsetAsync(p->v, 0, fb, p->stream));
-    return PE3D_OK;
+    return encode_tmap_v(p);
 }
 
 static int read_status(pe3d_plan_s* p) {
@@ -315,6 +342,7 @@ int pe3d_destroy(pe3d_plan_t p) {
     cudaStreamSynchronize(p->stream);
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
+    if (p->capture) cudaStreamDestroy(p->capture);
     void** bufs[] = {&p->w, &p->v, &p->u0stage, &p->outstage, &p->n2, &p->mz, &p->mB, &p->zsm,
                      &p->gscr, &p->sc, (void**)&p->slice_of_step, (void**)&p->status, (void**)&p->bar};
     for (void** b : bufs)

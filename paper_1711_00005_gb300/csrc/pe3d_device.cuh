@@ -18,6 +18,7 @@
 // pass from the scanned carry.  This exposes threads-per-system parallelism
 // without changing what elimination computes.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -93,14 +94,16 @@ __device__ __forceinline__ double2 shfl_down(double2 v, int d) {
 
 // Geometry of one scan: the chunks k = 0..K-1 of one system sit on lanes
 // (k % KW) * S + (lane offset of the system), KW = 32 / S chunks per warp, in
-// W = K / KW consecutive-k warps.  `scr` holds W entries private to this
-// system.  Every thread of the CTA must call this (it may __syncthreads).
+// W = K / KW consecutive-k warps.  Warp w's aggregate goes to scr[w * sstride]
+// (entries private to this system).  Every thread of the CTA must call this
+// (it may __syncthreads).
 struct ScanGeom {
-    int S;    // lane stride between consecutive chunks (1, 2, 4, ..., 32)
-    int KW;   // chunks per warp = 32 / S
-    int kw;   // this thread's chunk position inside its warp
-    int W;    // warps spanned by one system
-    int wk;   // this thread's warp position inside the system
+    int S;        // lane stride between consecutive chunks (1, 2, 4, ..., 32)
+    int KW;       // chunks per warp = 32 / S
+    int kw;       // this thread's chunk position inside its warp
+    int W;        // warps spanned by one system
+    int wk;       // this thread's warp position inside the system
+    int sstride;  // stride between warp entries in scr
 };
 
 // Exclusive carry of the scan, evaluated at zero: forward (FWD) returns the
@@ -108,8 +111,9 @@ struct ScanGeom {
 template <typename C, bool FWD>
 __device__ __forceinline__ C scan_carry(Aff<C> x, const ScanGeom& g, Aff<C>* scr) {
     const int pos = FWD ? g.kw : (g.KW - 1 - g.kw);
-#pragma unroll 1
-    for (int d = 1; d < g.KW; d <<= 1) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        if (d >= g.KW) break;
         Aff<C> o;
         if (FWD) { o.a = shfl_up(x.a, d * g.S); o.b = shfl_up(x.b, d * g.S); }
         else     { o.a = shfl_down(x.a, d * g.S); o.b = shfl_down(x.b, d * g.S); }
@@ -118,15 +122,87 @@ __device__ __forceinline__ C scan_carry(Aff<C> x, const ScanGeom& g, Aff<C>* scr
     Aff<C> P; P.a = cone<C>(); P.b = czero<C>();
     if (g.W > 1) {
         const bool last = FWD ? (g.kw == g.KW - 1) : (g.kw == 0);
-        if (last) scr[g.wk] = x;
+        if (last) scr[g.wk * g.sstride] = x;
         __syncthreads();
-        if (FWD) { for (int w = 0; w < g.wk; ++w) P = then(P, scr[w]); }
-        else     { for (int w = g.W - 1; w > g.wk; --w) P = then(P, scr[w]); }
+        if (FWD) { for (int w = 0; w < g.wk; ++w) P = then(P, scr[w * g.sstride]); }
+        else     { for (int w = g.W - 1; w > g.wk; --w) P = then(P, scr[w * g.sstride]); }
         __syncthreads();
     }
     const Aff<C> full = then(P, x);
     const C nb = FWD ? shfl_up(full.b, g.S) : shfl_down(full.b, g.S);
     return pos > 0 ? nb : P.b;
+}
+
+// ---------------------------------------------------------------------------
+// TMA (bulk and tensor copies global -> shared) completing on an mbarrier
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// 1-D bulk copy (16-B aligned addresses, size a multiple of 16 B)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+// 2-D tiled tensor copy; x (innermost) must be a multiple of 16 B in elements
+__device__ __forceinline__ void tma_g2s_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+// order this thread's generic-proxy view before its later async-proxy accesses
+__device__ __forceinline__ void fence_proxy_async_all() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+constexpr long long MBAR_SPIN_LIMIT = 1ll << 22;
+
+// Optional sub-step timestamps (build with -DPE3D_TRACE): thread 0 of each
+// CTA records clock64() into slot s of its row of pe3d_trace.
+#ifdef PE3D_TRACE
+constexpr int TRACE_SLOTS = 24;
+__device__ long long pe3d_trace[4096 * TRACE_SLOTS];
+#define PE3D_MARK(s) \
+    do { if (threadIdx.x == 0 && blockIdx.x < 4096) pe3d::pe3d_trace[blockIdx.x * pe3d::TRACE_SLOTS + (s)] = clock64(); } while (0)
+#else
+#define PE3D_MARK(s) do { } while (0)
+#endif
+
+// Bounded wait for an mbarrier phase.  On timeout it records the status,
+// waits once more (bounded) for the copies in flight, and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status, int code) {
+    for (long long i = 0; i < MBAR_SPIN_LIMIT; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    atomicExch(status, code);
+    for (long long i = 0; i < MBAR_SPIN_LIMIT; ++i)
+        if (mbar_try_wait(bar, parity)) break;
+    return false;
 }
 
 // ---------------------------------------------------------------------------

@@ -12,3 +12,12 @@ int batched_f32(int n, pe3d_plan_s* const* plans, const void* const* u0, const d
     return batched<float2>(n, plans, u0, r0, steps, stride, out);
 }
 }  // namespace pe3d_host
+
+#ifdef PE3D_TRACE
+// tracing builds only: copy the FP32 kernels' sub-step timestamps to the host
+extern "C" int pe3d_trace_read(void* host, size_t bytes) {
+    PE3D_CUDA(cudaDeviceSynchronize());
+    PE3D_CUDA(cudaMemcpyFromSymbol(host, pe3d::pe3d_trace, bytes));
+    return PE3D_OK;
+}
+#endif

@@ -1,6 +1,7 @@
 // pe3d_internal.h -- host-side plan structure shared by the C ABI and the
 // typed launch layers (FP32 and FP64 are compiled as separate units).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -25,12 +26,15 @@ struct pe3d_plan_s {
     int rc_every = 0;
     int timing = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaStream_t capture = nullptr;   // private stream for graph capture
     int64_t last_kernel_ns = 0;
     int64_t total_launches = 0;
 
     // layout (fixed once the medium is set)
     int T = 0, L = 0, ldz = 0, NG = 0;
     int TZ = 0, K = 0, Lt = 0, NtP = 0, tiles = 0;
+    int BY = 0, nload = 0, rowsB = 0;   // azimuth tile: TMA boxes of BY rows
+    CUtensorMap tmap_v;                 // 2-D view of v for the tile loads
 
     // device buffers (bytes are complex of the plan precision unless noted)
     void* w = nullptr;
@@ -92,5 +96,6 @@ int dev_alloc(pe3d_plan_s* p, void** ptr, size_t bytes);
 void dev_free(pe3d_plan_s* p, void** ptr, size_t bytes);
 int ensure_steps(pe3d_plan_s* p, int steps);
 int active_slice(const std::vector<double>& slice_r, double r);
+int encode_tmap_v(pe3d_plan_s* p);
 
 }  // namespace pe3d_host

@@ -33,11 +33,13 @@ constexpr int ST_TIMEOUT = -4;    // PE3D_ERR_TIMEOUT
 
 template <typename C>
 struct MarchArgs {
+    CUtensorMap tmap_v;         // v as 2-D (x: depth in 8-B units, y: azimuth)
     int Nz, Nt, ldz, periodic;
-    // phase A layout: T threads per depth system, chunk L, NG systems per CTA
+    // phase A layout: T threads per depth system, chunk L (odd), NG systems per CTA
     int T, L, NG;
-    // phase B layout: TZ depths per tile, K chunks of Lt azimuths, NtP = K*Lt
-    int TZ, K, Lt, NtP, tiles;
+    // phase B layout: TZ depths per tile, K chunks of Lt (odd) azimuths, NtP = K*Lt;
+    // the tile arrives as nload TMA boxes of BY rows; rowsB rows of shared memory
+    int TZ, K, Lt, NtP, tiles, BY, nload, rowsB;
     C* w;                       // [Nt][ldz]
     C* v;                       // [Nt][ldz]
     const C* mz;                // [slices][Nt][ldz] depth multipliers
@@ -55,204 +57,297 @@ struct MarchArgs {
     int j0, j1;                 // steps [j0, j1)
 };
 
+__host__ __device__ constexpr size_t align128(size_t x) { return (x + 127) & ~size_t(127); }
+
+// Compile-time maxima of the per-thread chunk lengths (odd); a plan's runtime
+// chunk is at most its kernel's maximum and shorter chunks are predicated.
+constexpr int CHUNK_MAX[4] = {5, 9, 17, 33};
+__host__ __device__ constexpr int chunk_class(int L) { return L <= 5 ? 0 : L <= 9 ? 1 : L <= 17 ? 2 : L <= 33 ? 3 : -1; }
+
+// shared memory: [0,128) mbarrier; phase A: NG groups of (w/v, mu) columns
+// then the scan scratch; phase B: tile, mu, z, scan scratch, SM factors
+template <typename C>
+__host__ __device__ inline size_t smemA_group(int ldz) { return align128((size_t)2 * ldz * sizeof(C)); }
 template <typename C>
 __host__ __device__ inline size_t smemA_bytes(int NG, int ldz, int T) {
-    return (size_t)NG * 3 * ldz * sizeof(C) + (size_t)NG * (T / 32) * sizeof(Aff<C>);
+    return 128 + (size_t)NG * smemA_group<C>(ldz) + align128((size_t)NG * (T / 32) * sizeof(Aff<C>));
 }
 template <typename C>
-__host__ __device__ inline size_t smemB_bytes(int NtP, int TZ) {
-    return ((size_t)NtP * TZ + 2 * (size_t)NtP) * sizeof(C) + (size_t)TZ * (NT / 32) * sizeof(Aff<C>)
-           + (size_t)TZ * sizeof(double2);
-}
+struct SmemB {
+    size_t tile, mu, z, scr, sf, total;
+    __host__ __device__ SmemB(int rowsB, int TZ, int NtP) {
+        size_t o = 128;
+        tile = o; o += align128((size_t)rowsB * TZ * sizeof(C));
+        mu = o;   o += align128((size_t)NtP * sizeof(C));
+        z = o;    o += align128((size_t)NtP * sizeof(C));
+        scr = o;  o += align128((size_t)TZ * (NT / 32) * sizeof(Aff<C>));
+        sf = o;   o += align128((size_t)2 * TZ * sizeof(double2));
+        total = o;
+    }
+};
+template <typename C>
+__host__ __device__ inline size_t smemB_bytes(int rowsB, int TZ, int NtP) { return SmemB<C>(rowsB, TZ, NtP).total; }
 
 // ---------------------------------------------------------------------------
-// phase A: depth systems m = base .. base+NG-1 (one group of T threads each)
+// phase A: depth systems m = base .. base+NG-1 (one group of T threads each);
+// lane k of a group owns elements k*L .. k*L+L-1 of its column (L <= LA).
+// Returns false (uniformly across the CTA) if a bounded wait gave up.
 // ---------------------------------------------------------------------------
-template <typename C>
-__device__ void phaseA(const MarchArgs<C>& P, int j, int base, unsigned char* smem) {
+template <typename C, int LA>
+__device__ bool phaseA(const MarchArgs<C>& P, int j, int base, unsigned char* smem, uint32_t& parity) {
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem);
     const int tid = threadIdx.x;
     const int gs = tid / P.T, k = tid - gs * P.T;
     const int m = base + gs;
     const bool active = m < P.Nt;
     const int ldz = P.ldz, L = P.L;
-    C* sw = reinterpret_cast<C*>(smem) + (size_t)gs * 3 * ldz;
-    C* sm = sw + ldz;
-    C* sg = sm + ldz;
-    Aff<C>* scr = reinterpret_cast<Aff<C>*>(reinterpret_cast<C*>(smem) + (size_t)P.NG * 3 * ldz) + gs * (P.T / 32);
+    const size_t gstride = smemA_group<C>(ldz);
+    C* sw = reinterpret_cast<C*>(smem + 128 + gs * gstride);   // w, overwritten by v
+    const C* sm = sw + ldz;
+    Aff<C>* scr = reinterpret_cast<Aff<C>*>(smem + 128 + P.NG * gstride) + gs * (P.T / 32);
 
-    // 1. stage the column of w and the slice's multipliers (16-B coalesced)
-    if (active) {
+    // 1. one thread stages every active group's column of w and of the slice's
+    //    multipliers with bulk copies (one round trip)
+    PE3D_MARK(0);
+    if (tid == 0) {
+        fence_proxy_async_all();
         const C* mz = P.mz + (long long)P.slice_of_step[j] * P.slice_stride;
-        const float4* gw = reinterpret_cast<const float4*>(P.w + (size_t)m * ldz);
-        const float4* gm = reinterpret_cast<const float4*>(mz + (size_t)m * ldz);
-        float4* s4w = reinterpret_cast<float4*>(sw);
-        float4* s4m = reinterpret_cast<float4*>(sm);
-        const int n16 = (int)(ldz * sizeof(C) / 16);
-        for (int i = k; i < n16; i += P.T) {
-            s4w[i] = __ldcg(gw + i);
-            s4m[i] = __ldg(gm + i);
+        const int nact = min(P.NG, P.Nt - base);
+        const uint32_t colb = (uint32_t)(ldz * sizeof(C));
+        mbar_arrive_expect_tx(mbar, 2u * nact * colb);
+        for (int g = 0; g < nact; ++g) {
+            C* dw = reinterpret_cast<C*>(smem + 128 + g * gstride);
+            bulk_g2s(dw, P.w + (size_t)(base + g) * ldz, colb, mbar);
+            bulk_g2s(dw + ldz, mz + (size_t)(base + g) * ldz, colb, mbar);
         }
     }
-    __syncthreads();
+    const bool ok = mbar_wait_bounded(mbar, parity, P.status, ST_TIMEOUT);
+    parity ^= 1u;
+    if (!__syncthreads_and(ok)) return false;
+    PE3D_MARK(1);
 
     ScanGeom geo;
-    geo.S = 1; geo.KW = 32; geo.kw = k & 31; geo.W = P.T >> 5; geo.wk = k >> 5;
-    const int b0 = k * L;
+    geo.S = 1; geo.KW = 32; geo.kw = k & 31; geo.W = P.T >> 5; geo.wk = k >> 5; geo.sstride = 1;
+    C* wk_ = sw + k * L;
+    const C* mk = sm + k * L;
+    // The chunk is held in registers; elements i >= L (only when L < LA) act
+    // as the identity map (mu = 1, w = 0), so every pass is branch-free.
+    const C one = cone<C>(), zero = czero<C>();
+    C wq[LA], mq[LA], gq[LA];
+#pragma unroll
+    for (int i = 0; i < LA; ++i) {
+        const int ii = min(i, L - 1);
+        wq[i] = i < L ? wk_[ii] : zero;
+        mq[i] = i < L ? mk[ii] : one;
+    }
 
     // 2. forward elimination: compose this chunk's maps g -> mu (g + w)
-    Aff<C> agg; agg.a = cone<C>(); agg.b = czero<C>();
-    for (int i = 0; i < L; ++i) {
-        const C mu = sm[b0 + i];
-        agg.b = cfma(mu, agg.b, cmul(mu, sw[b0 + i]));
-        agg.a = cmul(mu, agg.a);
+    Aff<C> agg; agg.a = one; agg.b = zero;
+#pragma unroll
+    for (int i = 0; i < LA; ++i) {
+        agg.b = cfma(mq[i], agg.b, cmul(mq[i], wq[i]));
+        agg.a = cmul(mq[i], agg.a);
     }
+    PE3D_MARK(2);
     C g = scan_carry<C, true>(agg, geo, scr);
-    for (int i = 0; i < L; ++i) {
-        const C mu = sm[b0 + i];
-        g = cfma(mu, g, cmul(mu, sw[b0 + i]));
-        sg[b0 + i] = g;
+    PE3D_MARK(3);
+#pragma unroll
+    for (int i = 0; i < LA; ++i) {
+        g = cfma(mq[i], g, cmul(mq[i], wq[i]));
+        gq[i] = i < L ? g : zero;
     }
     // 3. back substitution: y -> g + mu y, composed from the chunk's end
-    agg.a = cone<C>(); agg.b = czero<C>();
-    for (int i = L - 1; i >= 0; --i) {
-        const C mu = sm[b0 + i];
-        agg.b = cfma(mu, agg.b, sg[b0 + i]);
-        agg.a = cmul(mu, agg.a);
+    agg.a = one; agg.b = zero;
+#pragma unroll
+    for (int i = LA - 1; i >= 0; --i) {
+        agg.b = cfma(mq[i], agg.b, gq[i]);
+        agg.a = cmul(mq[i], agg.a);
     }
+    PE3D_MARK(4);
     C y = scan_carry<C, false>(agg, geo, scr);
-    for (int i = L - 1; i >= 0; --i) {
-        const C mu = sm[b0 + i];
-        y = cfma(mu, y, sg[b0 + i]);
-        sg[b0 + i] = cfma(P.c2p, y, cmul(P.c1, sw[b0 + i]));   // v_i
+    PE3D_MARK(5);
+    const C c1 = P.c1, c2p = P.c2p;
+#pragma unroll
+    for (int i = LA - 1; i >= 0; --i) {
+        y = cfma(mq[i], y, gq[i]);
+        const C v = cfma(c2p, y, cmul(c1, wq[i]));
+        if (i < L) wk_[i] = v;                              // v_i over w_i
     }
     __syncthreads();
+    PE3D_MARK(6);
 
     // 4. store v (16-B coalesced)
     if (active) {
         float4* gv = reinterpret_cast<float4*>(P.v + (size_t)m * ldz);
-        const float4* s4v = reinterpret_cast<const float4*>(sg);
+        const float4* s4v = reinterpret_cast<const float4*>(sw);
         const int n16 = (int)(ldz * sizeof(C) / 16);
         for (int i = k; i < n16; i += P.T) __stcg(gv + i, s4v[i]);
     }
+    PE3D_MARK(7);
+    return true;
 }
 
 // ---------------------------------------------------------------------------
-// phase B: azimuth systems for depths p0 .. p0+TZ-1 (tile `tile`)
+// phase B: azimuth systems for depths p0 .. p0+TZ-1 (tile `tile`); thread
+// (g, k) owns rows k*Lt .. k*Lt+Lt-1 of depth p0+g (Lt <= LB).
 // ---------------------------------------------------------------------------
-template <typename C>
-__device__ void phaseB(const MarchArgs<C>& P, int j, int tile, unsigned char* smem) {
+template <typename C, int LB>
+__device__ bool phaseB(const MarchArgs<C>& P, int j, int tile, unsigned char* smem, uint32_t& parity) {
     using R = typename real_of<C>::type;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem);
     const int tid = threadIdx.x;
     const int TZ = P.TZ, Nt = P.Nt, NtP = P.NtP, Lt = P.Lt, ldz = P.ldz;
-    const int g = tid % TZ, k = tid / TZ;
+    const int tzs = __ffs(TZ) - 1;                  // TZ is a power of two
+    const int g = tid & (TZ - 1), k = tid >> tzs;
     const int p0 = tile * TZ;
-    C* tl = reinterpret_cast<C*>(smem);          // [NtP][TZ]
-    C* smu = tl + (size_t)NtP * TZ;              // [NtP]
-    C* sz = smu + NtP;                           // [NtP]
-    Aff<C>* scr = reinterpret_cast<Aff<C>*>(sz + NtP) + g * (NT / 32);
-    double2* sf = reinterpret_cast<double2*>(reinterpret_cast<Aff<C>*>(sz + NtP) + TZ * (NT / 32));
+    const SmemB<C> lay(P.rowsB, TZ, NtP);
+    C* tl = reinterpret_cast<C*>(smem + lay.tile);    // [rowsB][TZ]
+    const C* smu = reinterpret_cast<const C*>(smem + lay.mu);
+    const C* sz = reinterpret_cast<const C*>(smem + lay.z);
+    Aff<C>* scr = reinterpret_cast<Aff<C>*>(smem + lay.scr) + g;
+    double2* sf = reinterpret_cast<double2*>(smem + lay.sf);
 
-    // 1. stage the tile of v (rows m < Nt; zero rows beyond) and the step's multipliers
-    {
-        const int upr = (int)(TZ * sizeof(C) / 16);     // 16-B units per row
-        float4* t4 = reinterpret_cast<float4*>(tl);
-        const int total = NtP * upr;
-        for (int i = tid; i < total; i += NT) {
-            const int row = i / upr, c = i - row * upr;
-            float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (row < Nt) val = __ldcg(reinterpret_cast<const float4*>(P.v + (size_t)row * ldz + p0) + c);
-            t4[i] = val;
-        }
-        const C* mB = P.mB + (size_t)j * NtP;
-        for (int i = tid; i < NtP; i += NT) smu[i] = __ldg(mB + i);
-        if (P.periodic) {
-            const C* zs = P.zsm + (size_t)j * NtP;
-            for (int i = tid; i < NtP; i += NT) sz[i] = __ldg(zs + i);
-        }
+    // 1. the tile of v (TMA boxes of BY rows; rows past Nt arrive as zeros),
+    //    the step's multipliers and, for a full circle, its SM vector
+    PE3D_MARK(8);
+    if (tid == 0) {
+        fence_proxy_async_all();
+        const uint32_t boxb = (uint32_t)(P.BY * TZ * sizeof(C));
+        const uint32_t rowb = (uint32_t)(NtP * sizeof(C));
+        mbar_arrive_expect_tx(mbar, P.nload * boxb + rowb * (P.periodic ? 2u : 1u));
+        const int x = p0 * (int)(sizeof(C) / 8);
+        for (int q = 0; q < P.nload; ++q)
+            tma_g2s_2d(tl + (size_t)q * P.BY * TZ, &P.tmap_v, x, q * P.BY, mbar);
+        bulk_g2s(const_cast<C*>(smu), P.mB + (size_t)j * NtP, rowb, mbar);
+        if (P.periodic) bulk_g2s(const_cast<C*>(sz), P.zsm + (size_t)j * NtP, rowb, mbar);
     }
-    __syncthreads();
+    {   // rows the boxes do not cover are zero
+        const int r0z = P.nload * P.BY;
+        for (int i = r0z * TZ + tid; i < NtP * TZ; i += NT) tl[i] = czero<C>();
+    }
+    const StepConst sc = P.sc[j];
+    const bool ok = mbar_wait_bounded(mbar, parity, P.status, ST_TIMEOUT);
+    parity ^= 1u;
+    if (!__syncthreads_and(ok)) return false;
+    PE3D_MARK(9);
 
     ScanGeom geo;
-    geo.S = TZ; geo.KW = 32 / TZ; geo.kw = k % geo.KW; geo.W = (NT / TZ) / geo.KW; geo.wk = k / geo.KW;
+    geo.S = TZ; geo.KW = 32 >> tzs; geo.kw = k & (geo.KW - 1); geo.W = NT / 32; geo.wk = k / geo.KW;
+    geo.sstride = TZ;
     const int r0 = k * Lt;
+    C* tk = tl + (size_t)r0 * TZ + g;                 // row r0 + i at tk[i * TZ]
+    const C* mk = smu + r0;
+    // rows i >= Lt of the register chunk act as the identity (mu = 1, v = 0)
+    const C one = cone<C>(), zero = czero<C>();
+    C vq[LB], mq[LB];
+#pragma unroll
+    for (int i = 0; i < LB; ++i) {
+        const int ii = min(i, Lt - 1);
+        vq[i] = i < Lt ? tk[ii * TZ] : zero;
+        mq[i] = i < Lt ? mk[ii] : one;
+    }
 
-    Aff<C> agg; agg.a = cone<C>(); agg.b = czero<C>();
-    for (int i = 0; i < Lt; ++i) {
-        const C mu = smu[r0 + i];
-        agg.b = cfma(mu, agg.b, cmul(mu, tl[(r0 + i) * TZ + g]));
-        agg.a = cmul(mu, agg.a);
+    Aff<C> agg; agg.a = one; agg.b = zero;
+#pragma unroll
+    for (int i = 0; i < LB; ++i) {
+        agg.b = cfma(mq[i], agg.b, cmul(mq[i], vq[i]));
+        agg.a = cmul(mq[i], agg.a);
     }
+    PE3D_MARK(10);
     C gg = scan_carry<C, true>(agg, geo, scr);
-    for (int i = 0; i < Lt; ++i) {
-        const C mu = smu[r0 + i];
-        C* e = &tl[(r0 + i) * TZ + g];
-        gg = cfma(mu, gg, cmul(mu, *e));
-        *e = gg;
+    PE3D_MARK(11);
+#pragma unroll
+    for (int i = 0; i < LB; ++i) {
+        gg = cfma(mq[i], gg, cmul(mq[i], vq[i]));
+        vq[i] = i < Lt ? gg : zero;
     }
-    agg.a = cone<C>(); agg.b = czero<C>();
-    for (int i = Lt - 1; i >= 0; --i) {
-        const C mu = smu[r0 + i];
-        agg.b = cfma(mu, agg.b, tl[(r0 + i) * TZ + g]);
-        agg.a = cmul(mu, agg.a);
+    agg.a = one; agg.b = zero;
+#pragma unroll
+    for (int i = LB - 1; i >= 0; --i) {
+        agg.b = cfma(mq[i], agg.b, vq[i]);
+        agg.a = cmul(mq[i], agg.a);
     }
+    PE3D_MARK(12);
     C y = scan_carry<C, false>(agg, geo, scr);
-    const StepConst sc = P.sc[j];
+    PE3D_MARK(13);
     const C nbinv = from64<C>(sc.nbinv);
-    for (int i = Lt - 1; i >= 0; --i) {
-        const C mu = smu[r0 + i];
-        C* e = &tl[(r0 + i) * TZ + g];
-        y = cfma(mu, y, *e);
-        *e = cmul(nbinv, y);
+#pragma unroll
+    for (int i = LB - 1; i >= 0; --i) {
+        y = cfma(mq[i], y, vq[i]);
+        vq[i] = cmul(nbinv, y);
     }
-    __syncthreads();
 
     if (P.periodic) {
         // Sherman-Morrison: u = y - f z, f = (y_0 + (e/gamma) y_{N-1}) xi, in FP64
-        if (k == 0) {
-            const double2 y0 = to64(tl[g]);
-            const double2 yn = to64(tl[(Nt - 1) * TZ + g]);
-            sf[g] = cmul(cadd(y0, cmul(sc.bg, yn)), sc.xi);
-        }
+        const int rl = Nt - 1 - r0;                  // local index of row Nt-1, if ours
+        if (k == 0) sf[g] = to64(vq[0]);
+#pragma unroll
+        for (int i = 0; i < LB; ++i)
+            if (i < Lt && i == rl) sf[TZ + g] = to64(vq[i]);
         __syncthreads();
-        const C f = from64<C>(sf[g]);
-        for (int i = 0; i < Lt; ++i) {
-            const int row = r0 + i;
-            C* e = &tl[row * TZ + g];
-            *e = csub(*e, cmul(f, sz[row]));
+        const C f = from64<C>(cmul(cadd(sf[g], cmul(sc.bg, sf[TZ + g])), sc.xi));
+#pragma unroll
+        for (int i = 0; i < LB; ++i) {
+            const int ii = min(i, Lt - 1);
+            vq[i] = csub(vq[i], cmul(f, sz[r0 + ii]));
         }
-        __syncthreads();
     }
-
-    // next step's azimuth stencil, field store and optional snapshot
+    // the solved field back into the tile, then the next step's azimuth
+    // stencil, the field store and the optional snapshot
+#pragma unroll
+    for (int i = 0; i < LB; ++i)
+        if (i < Lt) tk[i * TZ] = vq[i];
+    __syncthreads();
+    PE3D_MARK(14);
     const C q = from64<C>(sc.qnext);
     const bool snap = P.snap != nullptr && ((j + 1) % P.stride) == 0;
-    C* sp = snap ? P.snap + (size_t)((j + 1) / P.stride - 1) * Nt * P.snap_ld : nullptr;
+    C* sp = snap ? P.snap + (size_t)((j + 1) / P.stride - 1) * Nt * P.snap_ld + p0 + g : nullptr;
+    const bool col_ok = p0 + g < P.Nz;
+    // neighbours across the chunk edges: row r0-1 and row r0+Lt; the row after
+    // Nt-1 is row 0 on a full circle and the zero ghost between walls
+    const C wrap_up = P.periodic ? tl[g] : zero;
+    const C wrap_dn = P.periodic ? tl[(size_t)(Nt - 1) * TZ + g] : zero;
+    const C dn = r0 > 0 ? tl[(size_t)(r0 - 1) * TZ + g] : wrap_dn;
+    const int rend = min(r0 + Lt, P.rowsB - 1);
+    const C up = tl[(size_t)rend * TZ + g];
     const C two = cmake((R)2, (R)0);
-    for (int i = tid; i < Nt * TZ; i += NT) {
-        const int row = i / TZ, gi = i - row * TZ;
-        const C u = tl[i];
-        C up, dn;
-        if (row + 1 < Nt) up = tl[i + TZ]; else up = P.periodic ? tl[gi] : czero<C>();
-        if (row > 0) dn = tl[i - TZ]; else dn = P.periodic ? tl[(Nt - 1) * TZ + gi] : czero<C>();
-        const C lap = csub(cadd(up, dn), cmul(two, u));
-        __stcg(P.w + (size_t)row * ldz + p0 + gi, cfma(q, lap, u));
-        if (snap && p0 + gi < P.Nz) sp[(size_t)row * P.snap_ld + p0 + gi] = u;
+    C* wcol = P.w + (size_t)r0 * ldz + p0 + g;
+#pragma unroll
+    for (int i = 0; i < LB; ++i) {
+        const int row = r0 + i;
+        const C nxt = (row + 1 == Nt) ? wrap_up : (i + 1 < LB ? vq[(i + 1) % LB] : up);
+        const C nx2 = (i + 1 == Lt && row + 1 != Nt) ? up : nxt;
+        const C prv = (i == 0) ? dn : vq[(i + LB - 1) % LB];
+        const C lap = csub(cadd(nx2, prv), cmul(two, vq[i]));
+        const C wn = cfma(q, lap, vq[i]);
+        if (i < Lt && row < Nt) {
+            __stcg(wcol + (size_t)i * ldz, wn);
+            if (snap && col_ok) sp[(size_t)row * P.snap_ld] = vq[i];
+        }
     }
+    PE3D_MARK(15);
+    return true;
 }
 
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
-template <typename C>
-__global__ void __launch_bounds__(NT) k_phaseA(MarchArgs<C> P, int j) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    phaseA(P, j, blockIdx.x * P.NG, smem);
+template <typename C, int LA>
+__global__ void __launch_bounds__(NT) k_phaseA(const __grid_constant__ MarchArgs<C> P, int j) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t*>(smem), 1);
+    __syncthreads();
+    uint32_t parity = 0;
+    phaseA<C, LA>(P, j, blockIdx.x * P.NG, smem, parity);
 }
 
-template <typename C>
-__global__ void __launch_bounds__(NT) k_phaseB(MarchArgs<C> P, int j) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    phaseB(P, j, blockIdx.x, smem);
+template <typename C, int LB>
+__global__ void __launch_bounds__(NT) k_phaseB(const __grid_constant__ MarchArgs<C> P, int j) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t*>(smem), 1);
+    __syncthreads();
+    uint32_t parity = 0;
+    phaseB<C, LB>(P, j, blockIdx.x, smem, parity);
 }
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -271,6 +366,7 @@ __device__ __forceinline__ int ld_relaxed(const int* p) {
 // an error, it records PE3D_ERR_TIMEOUT and returns false.
 __device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target, int* status) {
     __shared__ int s_ok;
+    asm volatile("fence.proxy.async.global;" ::: "memory");
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -283,6 +379,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target, int
             if (spins > 32) __nanosleep(32);
         }
         __threadfence();
+        asm volatile("fence.proxy.async.global;" ::: "memory");
         s_ok = ok;
     }
     __syncthreads();
@@ -290,23 +387,30 @@ __device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target, int
 }
 
 // The whole march in one cooperative launch: two grid barriers per step.
-template <typename C>
-__global__ void __launch_bounds__(NT) k_march_persistent(MarchArgs<C> P) {
-    extern __shared__ __align__(16) unsigned char smem[];
+template <typename C, int LA, int LB>
+__global__ void __launch_bounds__(NT) k_march_persistent(const __grid_constant__ MarchArgs<C> P) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t*>(smem), 1);
+    __syncthreads();
+    uint32_t parity = 0;
     const unsigned G = gridDim.x;
     unsigned nb = 0;
     const int unitsA = (P.Nt + P.NG - 1) / P.NG;
     for (int j = P.j0; j < P.j1; ++j) {
         for (int u = blockIdx.x; u < unitsA; u += G) {
-            phaseA(P, j, u * P.NG, smem);
+            if (!phaseA<C, LA>(P, j, u * P.NG, smem, parity)) return;
             __syncthreads();
         }
+        PE3D_MARK(16);
         if (!grid_barrier(P.bar, (++nb) * G, P.status)) return;
+        PE3D_MARK(17);
         for (int t = blockIdx.x; t < P.tiles; t += G) {
-            phaseB(P, j, t, smem);
+            if (!phaseB<C, LB>(P, j, t, smem, parity)) return;
             __syncthreads();
         }
+        PE3D_MARK(18);
         if (!grid_barrier(P.bar, (++nb) * G, P.status)) return;
+        PE3D_MARK(19);
     }
 }
 

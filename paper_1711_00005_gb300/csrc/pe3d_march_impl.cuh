@@ -19,10 +19,26 @@ inline double2 h_div(double2 a, double2 b) {
     return d2((a.x * b.x + a.y * b.y) / n, (a.y * b.x - a.x * b.y) / n);
 }
 
-// Depth-system and azimuth-tile layout.  Depth: T threads per system (a
-// multiple of 32), chunk L odd (so lane k's element k*L+i falls in distinct
-// shared-memory banks), ldz = T*L >= Nz.  Azimuth: TZ depths per tile and
-// K = 256/TZ chunks of Lt = ceil(Nt/K) azimuths.
+// Depth-system and azimuth-tile layout.  Depth: T threads per system (32,
+// 64, 128 or 256), chunk L odd (so lane k's element k*L+i falls in distinct
+// shared-memory banks), ldz = T*L >= Nz; by default the smallest T whose chunk
+// is at most 9.  Azimuth: TZ depths per tile and K = 256/TZ chunks of Lt
+// azimuths (odd for the same reason), NtP = K*Lt; the tile arrives as nload
+// TMA boxes of BY <= 256 rows, BY rounded so that every box starts on a
+// 128-byte boundary of shared memory (required by tensor copies).
+inline int odd_ceil(int a, int b) {
+    int q = (a + b - 1) / b;
+    return (q & 1) ? q : q + 1;
+}
+
+inline int box_rows(int Nt, int nload, int row_bytes) {
+    int g = 128, r = row_bytes;
+    while (r) { const int t = g % r; g = r; r = t; }   // gcd(128, row_bytes)
+    const int mult = 128 / g;
+    const int by = (Nt + nload - 1) / nload;
+    return (by + mult - 1) / mult * mult;
+}
+
 template <typename C>
 int layout_choose(pe3d_plan_s* p) {
     const int cand[4] = {32, 64, 128, 256};
@@ -30,21 +46,15 @@ int layout_choose(pe3d_plan_s* p) {
     for (int ci = 0; ci < 4; ++ci) {
         const int T = cand[ci];
         if (p->zthreads && T != p->zthreads) continue;
-        int L = (p->Nz + T - 1) / T;
-        if ((L & 1) == 0) ++L;
-        const int ldz = T * L;
-        const int NG = NT / T;
-        if (smemA_bytes<C>(NG, ldz, T) > SMEM_BUDGET) continue;
-        if (p->zthreads) { best = T; break; }
-        if (best < 0) best = T;
-        // smallest T whose chunk is short enough; else keep growing T
-        if (L <= 17) { best = T; break; }
+        const int L = odd_ceil(p->Nz, T);
+        if (L > 33 || smemA_bytes<C>(NT / T, T * L, T) > SMEM_BUDGET) continue;
         best = T;
+        if (p->zthreads || L <= 9) break;
     }
-    if (best < 0) return fail(PE3D_ERR_ARG, "depth systems too long for the shared-memory budget");
+    if (best < 0) return fail(PE3D_ERR_ARG, "depth systems too long (at most 256 threads x 33 points) or too "
+                                            "large for the shared-memory budget");
     p->T = best;
-    p->L = (p->Nz + best - 1) / best;
-    if ((p->L & 1) == 0) ++p->L;
+    p->L = odd_ceil(p->Nz, best);
     p->ldz = p->T * p->L;
     p->NG = NT / p->T;
 
@@ -54,16 +64,25 @@ int layout_choose(pe3d_plan_s* p) {
         const int TZ = tz_cand[ci];
         if (p->ttile && TZ != p->ttile) continue;
         const int K = NT / TZ;
-        const int Lt = (p->Nt + K - 1) / K;
-        if (smemB_bytes<C>(K * Lt, TZ) > SMEM_BUDGET) continue;
+        const int Lt = odd_ceil(p->Nt, K);
+        const int nload = (p->Nt + 255) / 256;
+        const int BY = box_rows(p->Nt, nload, (int)(TZ * sizeof(C)));
+        const int rowsB = std::max(K * Lt, nload * BY);
+        if (Lt > 33 || smemB_bytes<C>(rowsB, TZ, K * Lt) > SMEM_BUDGET) continue;
         tz = TZ;
         break;
     }
-    if (tz < 0) return fail(PE3D_ERR_ARG, "azimuth systems too long for the shared-memory budget");
+    if (tz < 0) return fail(PE3D_ERR_ARG, "azimuth systems too long (at most 33 points per thread) or the tile "
+                                          "too large for the shared-memory budget");
     p->TZ = tz;
     p->K = NT / tz;
-    p->Lt = (p->Nt + p->K - 1) / p->K;
+    p->Lt = odd_ceil(p->Nt, p->K);
     p->NtP = p->K * p->Lt;
+    p->nload = (p->Nt + 255) / 256;
+    p->BY = box_rows(p->Nt, p->nload, (int)(tz * sizeof(C)));
+    p->rowsB = std::max(p->NtP, p->nload * p->BY);
+    if (p->BY > 256 || ((size_t)p->BY * tz * sizeof(C)) % 128 != 0 || (size_t)(p->nload - 1) * p->BY >= (size_t)p->Nt)
+        return fail(PE3D_ERR_ARG, "internal: azimuth tile boxes not 128-byte aligned");
     p->tiles = (p->Nz + tz - 1) / tz;
     return PE3D_OK;
 }
@@ -86,9 +105,11 @@ int setupA(pe3d_plan_s* p) {
 
 template <typename C>
 void fill_args(pe3d_plan_s* p, MarchArgs<C>& A) {
+    A.tmap_v = p->tmap_v;
     A.Nz = p->Nz; A.Nt = p->Nt; A.ldz = p->ldz; A.periodic = p->boundary == PE3D_PERIODIC;
     A.T = p->T; A.L = p->L; A.NG = p->NG;
     A.TZ = p->TZ; A.K = p->K; A.Lt = p->Lt; A.NtP = p->NtP; A.tiles = p->tiles;
+    A.BY = p->BY; A.nload = p->nload; A.rowsB = p->rowsB;
     A.w = reinterpret_cast<C*>(p->w);
     A.v = reinterpret_cast<C*>(p->v);
     A.mz = reinterpret_cast<const C*>(p->mz);
@@ -113,19 +134,49 @@ void fill_args(pe3d_plan_s* p, MarchArgs<C>& A) {
     A.j0 = 0; A.j1 = 0;
 }
 
+// every compiled (depth chunk, azimuth chunk) specialisation
+template <typename C>
+struct KernelTable {
+    const void* A[4];
+    const void* B[4];
+    const void* persist[4][4];
+    KernelTable() {
+        A[0] = (const void*)k_phaseA<C, 5>;  A[1] = (const void*)k_phaseA<C, 9>;
+        A[2] = (const void*)k_phaseA<C, 17>; A[3] = (const void*)k_phaseA<C, 33>;
+        B[0] = (const void*)k_phaseB<C, 5>;  B[1] = (const void*)k_phaseB<C, 9>;
+        B[2] = (const void*)k_phaseB<C, 17>; B[3] = (const void*)k_phaseB<C, 33>;
+#define PE3D_P(a, b) persist[a][b] = (const void*)k_march_persistent<C, CHUNK_MAX[a], CHUNK_MAX[b]>
+        PE3D_P(0, 0); PE3D_P(0, 1); PE3D_P(0, 2); PE3D_P(0, 3);
+        PE3D_P(1, 0); PE3D_P(1, 1); PE3D_P(1, 2); PE3D_P(1, 3);
+        PE3D_P(2, 0); PE3D_P(2, 1); PE3D_P(2, 2); PE3D_P(2, 3);
+        PE3D_P(3, 0); PE3D_P(3, 1); PE3D_P(3, 2); PE3D_P(3, 3);
+#undef PE3D_P
+    }
+};
+
+template <typename C>
+const KernelTable<C>& kernels() {
+    static const KernelTable<C> t;
+    return t;
+}
+
 template <typename C>
 size_t smem_persistent(const pe3d_plan_s* p) {
-    return std::max(smemA_bytes<C>(p->NG, p->ldz, p->T), smemB_bytes<C>(p->NtP, p->TZ));
+    return std::max(smemA_bytes<C>(p->NG, p->ldz, p->T), smemB_bytes<C>(p->rowsB, p->TZ, p->NtP));
 }
 
 template <typename C>
 int prepare_kernels(const pe3d_plan_s* p) {
     static bool done = false;
     if (!done) {
-        PE3D_CUDA(cudaFuncSetAttribute(k_phaseA<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BUDGET));
-        PE3D_CUDA(cudaFuncSetAttribute(k_phaseB<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BUDGET));
-        PE3D_CUDA(cudaFuncSetAttribute(k_march_persistent<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)SMEM_BUDGET));
+        const KernelTable<C>& t = kernels<C>();
+        for (int a = 0; a < 4; ++a) {
+            PE3D_CUDA(cudaFuncSetAttribute(t.A[a], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BUDGET));
+            PE3D_CUDA(cudaFuncSetAttribute(t.B[a], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BUDGET));
+            for (int b = 0; b < 4; ++b)
+                PE3D_CUDA(cudaFuncSetAttribute(t.persist[a][b], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)SMEM_BUDGET));
+        }
         done = true;
     }
     (void)p;
@@ -164,7 +215,8 @@ int launch_prologue(pe3d_plan_s* p, const void* u0_dev, double r0) {
 template <typename C>
 int persistent_grid(const pe3d_plan_s* p, int* grid) {
     int nb = 0;
-    PE3D_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_march_persistent<C>, NT, smem_persistent<C>(p)));
+    const void* fn = kernels<C>().persist[chunk_class(p->L)][chunk_class(p->Lt)];
+    PE3D_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, NT, smem_persistent<C>(p)));
     if (nb < 1) return fail(PE3D_ERR_ARG, "persistent kernel does not fit on an SM");
     const int unitsA = (p->Nt + p->NG - 1) / p->NG;
     *grid = std::min(nb * p->num_sms, std::max(unitsA, p->tiles));
@@ -178,7 +230,9 @@ int run_steps(pe3d_plan_s* p, MarchArgs<C>& A, int steps) {
     p->last_exec = exec;
     const int unitsA = (p->Nt + p->NG - 1) / p->NG;
     const size_t sA = smemA_bytes<C>(p->NG, p->ldz, p->T);
-    const size_t sB = smemB_bytes<C>(p->NtP, p->TZ);
+    const size_t sB = smemB_bytes<C>(p->rowsB, p->TZ, p->NtP);
+    const KernelTable<C>& kt = kernels<C>();
+    const int ca = chunk_class(p->L), cb = chunk_class(p->Lt);
     if (steps == 0) { p->last_launches = 0; return PE3D_OK; }
     if (p->timing) PE3D_CUDA(cudaEventRecord(p->ev0, p->stream));
     if (exec == PE3D_EXEC_PERSISTENT) {
@@ -188,23 +242,30 @@ int run_steps(pe3d_plan_s* p, MarchArgs<C>& A, int steps) {
         PE3D_CUDA(cudaMemsetAsync(p->bar, 0, sizeof(unsigned), p->stream));
         A.j0 = 0; A.j1 = steps;
         void* args[] = {&A};
-        PE3D_CUDA(cudaLaunchCooperativeKernel((const void*)k_march_persistent<C>, dim3(grid), dim3(NT), args,
+        PE3D_CUDA(cudaLaunchCooperativeKernel(kt.persist[ca][cb], dim3(grid), dim3(NT), args,
                                               smem_persistent<C>(p), p->stream));
         p->last_grid = grid;
         p->last_launches = 1;
         if (p->timing) PE3D_CUDA(cudaEventRecord(p->ev1, p->stream));
         return PE3D_OK;
     }
-    cudaGraph_t graph = nullptr;
-    if (exec == PE3D_EXEC_GRAPH)
-        PE3D_CUDA(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
-    for (int j = 0; j < steps; ++j) {
-        k_phaseA<C><<<unitsA, NT, sA, p->stream>>>(A, j);
-        k_phaseB<C><<<p->tiles, NT, sB, p->stream>>>(A, j);
-    }
-    cudaError_t e = cudaGetLastError();
+    // graph mode: record the launches on a private stream (the caller's may be
+    // the legacy default stream, which cannot be captured), replay on the plan's
+    cudaStream_t ls = p->stream;
     if (exec == PE3D_EXEC_GRAPH) {
-        cudaError_t e2 = cudaStreamEndCapture(p->stream, &graph);
+        if (!p->capture) PE3D_CUDA(cudaStreamCreateWithFlags(&p->capture, cudaStreamNonBlocking));
+        ls = p->capture;
+        PE3D_CUDA(cudaStreamBeginCapture(ls, cudaStreamCaptureModeThreadLocal));
+    }
+    cudaError_t e = cudaSuccess;
+    for (int j = 0; j < steps && e == cudaSuccess; ++j) {
+        void* args[] = {&A, &j};
+        e = cudaLaunchKernel(kt.A[ca], dim3(unitsA), dim3(NT), args, sA, ls);
+        if (e == cudaSuccess) e = cudaLaunchKernel(kt.B[cb], dim3(p->tiles), dim3(NT), args, sB, ls);
+    }
+    if (exec == PE3D_EXEC_GRAPH) {
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(ls, &graph);
         if (e == cudaSuccess) e = e2;
         if (e == cudaSuccess) {
             cudaGraphExec_t ge = nullptr;

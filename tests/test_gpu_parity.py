@@ -94,6 +94,27 @@ def test_layouts_and_exec_modes(P, oracle_lib, zthreads, ttile, exec_mode):
     assert relerrs(got, ref).max() < TOL64
 
 
+@pytest.mark.parametrize("Nt", [257, 520, 1024])
+@pytest.mark.parametrize("ttile", [8, 16, 32])
+@pytest.mark.parametrize("fp32", [False, True], ids=["fp64", "fp32"])
+def test_multi_box_azimuth_tiles(P, oracle_lib, Nt, ttile, fp32):
+    """Ntheta > 256: the azimuth tile arrives in several TMA boxes."""
+    wl = workloads.random_case(37, Nt, periodic=(Nt != 520), K=2, steps=4, seed=Nt + ttile, stride=2)
+    tile_bytes = Nt * ttile * (8 if fp32 else 16)
+    chunk = -(-Nt // (256 // ttile))
+    if tile_bytes > 200 * 1024 or chunk + (1 - chunk % 2) > 33:
+        # the requested tile does not fit in shared memory, or its per-thread
+        # chunk exceeds the compiled maximum (33): refused, not run
+        with pytest.raises(P.PE3DError) as e:
+            gpu_march(P, wl, fp32=fp32, ttile=ttile)
+        assert e.value.code == P.PE3D_ERR_ARG and "shared-memory" in str(e.value)
+        return
+    ref = oracle_lib.march(wl.grid, wl.n2, wl.slice_r, wl.u0)
+    got, info = gpu_march(P, wl, fp32=fp32, ttile=ttile)
+    assert info["ttile"] == ttile
+    assert relerrs(got, ref).max() < (TOL32 if fp32 else TOL64)
+
+
 @pytest.mark.parametrize("fp32", [False, True], ids=["fp64", "fp32"])
 def test_exec_modes_bitwise_equal(P, fp32):
     """The same kernels in one persistent launch, a launch loop or a graph give
