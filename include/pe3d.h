@@ -149,6 +149,34 @@ int pe3d_autotune(pe3d_plan_t plan, double r0, int steps);
 int pe3d_march_batched(int n, const pe3d_plan_t *plans, const void *const *u0, const double *r0,
                        const int *steps, const int *out_stride, void *const *out);
 
+/* Allocation-free march.  The paper has no counterpart: this entry point is
+ * for callers that cannot allocate device memory while they run -- a real-time
+ * sonar or tracking loop that fixes its GPU memory at start-up and cannot take
+ * cudaMalloc's implicit synchronisation or a mid-run out-of-memory error, or an
+ * application whose own allocator owns the device heap.  It computes exactly
+ * what pe3d_plan + pe3d_set_medium + pe3d_march compute (persistent launch,
+ * default layout), but every intermediate lives in one file-scope device array
+ * of PE3D_STATIC_SCRATCH_BYTES, present on every GPU that loads the library
+ * until the process exits; it calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *   Arguments mean what they mean in pe3d_plan / pe3d_set_medium / pe3d_march;
+ *   n2, u0 and out must be device memory, slice_r host memory, K <= 256.
+ *   A march whose scratch (fields, coefficients of all K slices, per-step
+ *   tables) exceeds PE3D_STATIC_SCRATCH_BYTES is rejected with PE3D_ERR_ARG and
+ *   a message giving the size it needs.
+ *   The first call on a device looks up the array's device address (module
+ *   load) and caches it: make that first call before any CUDA graph capture.
+ *   Every call reuses the same array and leaves its contents behind; each call
+ *   clears what must start at zero.  Calls that overlap on the GPU (two host
+ *   threads, or two streams) race on the array: serialise them.  The call
+ *   returns after its stream has finished the march.
+ * Errors: PE3D_ERR_ARG, PE3D_ERR_SINGULAR, PE3D_ERR_TIMEOUT, PE3D_ERR_CUDA. */
+#define PE3D_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+#define PE3D_STATIC_MAX_SLICES 256
+int pe3d_march_static(int Nz, int Ntheta, double dz, double dtheta, double dr, double k0, int boundary,
+                      int precision, const void *n2, const double *slice_r, int K, const void *u0, double r0,
+                      int steps, int out_stride, void *out, void *cuda_stream);
+
 /* Message for the calling thread's most recent failed call ("" if none). */
 const char *pe3d_last_error(void);
 

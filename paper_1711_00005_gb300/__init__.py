@@ -86,6 +86,10 @@ _SIGS = {
                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "pe3d_last_error": ([], ctypes.c_char_p),
+    "pe3d_march_static": ([ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                           ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                           ctypes.c_int, ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                           ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "pe3d_server_create": ([ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)],
                            ctypes.c_int),
     "pe3d_submit": ([ctypes.c_void_p, ctypes.POINTER(pe3d_request), ctypes.POINTER(ctypes.c_uint64)],
@@ -212,6 +216,20 @@ def pe3d_march_batched(plans: Sequence, u0s: Sequence, r0s: Sequence[float], ste
     D = (ctypes.c_int * n)(*[int(x) for x in out_strides])
     _check(load_library().pe3d_march_batched(n, P, U, R, S, D, O))
     del keep
+
+
+def pe3d_march_static(Nz: int, Ntheta: int, dz: float, dtheta: float, dr: float, k0: float, boundary: int,
+                      precision: int, n2, slice_r, u0, r0: float, steps: int, out_stride: int, out,
+                      cuda_stream=None) -> None:
+    """The allocation-free march (device n2, u0 and out); see include/pe3d.h."""
+    pn, _, kn = _ptr(n2)
+    pu, _, ku = _ptr(u0)
+    po, _, ko = _ptr(out)
+    r = np.ascontiguousarray(slice_r, dtype=np.float64)
+    _check(load_library().pe3d_march_static(Nz, Ntheta, dz, dtheta, dr, k0, boundary, precision, pn,
+                                            ctypes.c_void_p(r.ctypes.data), len(r), pu, float(r0), int(steps),
+                                            int(out_stride), po, _stream_handle(cuda_stream)))
+    del kn, ku, ko
 
 
 def pe3d_last_error() -> str:

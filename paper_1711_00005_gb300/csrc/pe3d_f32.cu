@@ -11,6 +11,17 @@ int batched_f32(int n, pe3d_plan_s* const* plans, const void* const* u0, const d
                 const int* stride, void* const* out) {
     return batched<float2>(n, plans, u0, r0, steps, stride, out);
 }
+int static_kernels_f32(StaticKernels* k) {
+    int rc = prepare_kernels<float2>(nullptr);
+    if (rc) return rc;
+    k->setupA = (const void*)k_setupA<float2>;
+    k->setupB = (const void*)k_setupB<float2>;
+    k->prologue = (const void*)k_prologue<float2>;
+    const KernelTable<float2>& t = kernels<float2>();
+    for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) k->persist[a][b] = t.persist[a][b];
+    return PE3D_OK;
+}
 }  // namespace pe3d_host
 
 #ifdef PE3D_TRACE

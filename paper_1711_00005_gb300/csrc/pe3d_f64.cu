@@ -11,4 +11,15 @@ int batched_f64(int n, pe3d_plan_s* const* plans, const void* const* u0, const d
                 const int* stride, void* const* out) {
     return batched<double2>(n, plans, u0, r0, steps, stride, out);
 }
+int static_kernels_f64(StaticKernels* k) {
+    int rc = prepare_kernels<double2>(nullptr);
+    if (rc) return rc;
+    k->setupA = (const void*)k_setupA<double2>;
+    k->setupB = (const void*)k_setupB<double2>;
+    k->prologue = (const void*)k_prologue<double2>;
+    const KernelTable<double2>& t = kernels<double2>();
+    for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) k->persist[a][b] = t.persist[a][b];
+    return PE3D_OK;
+}
 }  // namespace pe3d_host

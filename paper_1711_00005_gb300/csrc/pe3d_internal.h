@@ -91,6 +91,16 @@ int batched_f32(int n, pe3d_plan_s* const* plans, const void* const* u0, const d
 int batched_f64(int n, pe3d_plan_s* const* plans, const void* const* u0, const double* r0, const int* steps,
                 const int* stride, void* const* out);
 
+// the compiled kernels of one precision, for launch by pointer
+struct StaticKernels {
+    const void* setupA;
+    const void* setupB;
+    const void* prologue;
+    const void* persist[4][4];
+};
+int static_kernels_f32(StaticKernels* k);   // also sets their shared-memory limits
+int static_kernels_f64(StaticKernels* k);
+
 // shared helpers (pe3d_api.cu)
 int dev_alloc(pe3d_plan_s* p, void** ptr, size_t bytes);
 void dev_free(pe3d_plan_s* p, void** ptr, size_t bytes);
