@@ -1,0 +1,123 @@
+// pe3d_batch_impl.cuh -- typed host layer of the batched march (included once per precision).
+#pragma once
+#include <algorithm>
+#include <vector>
+
+#include "pe3d_march_impl.cuh"
+
+namespace pe3d_host {
+using namespace pe3d;
+
+// compiled (depth chunk, azimuth chunk) classes of the batched kernel: chunks
+// shorter than the class maximum are predicated
+template <typename C>
+struct BatchTable {
+    const void* k[3][3];
+    BatchTable() {
+#define PE3D_B(a, b) k[a][b] = (const void*)k_march_batched<C, CHUNK_MAX[a + 1], CHUNK_MAX[b + 1]>
+        PE3D_B(0, 0); PE3D_B(0, 1); PE3D_B(0, 2);
+        PE3D_B(1, 0); PE3D_B(1, 1); PE3D_B(1, 2);
+        PE3D_B(2, 0); PE3D_B(2, 1); PE3D_B(2, 2);
+#undef PE3D_B
+    }
+};
+
+template <typename C>
+const BatchTable<C>& batch_kernels() {
+    static const BatchTable<C> t;
+    static bool attr = false;
+    if (!attr) {
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                cudaFuncSetAttribute(t.k[a][b], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BUDGET);
+        attr = true;
+    }
+    return t;
+}
+
+inline int batch_class(int L) { return std::max(0, chunk_class(L) - 1); }
+
+// Advance every march i from its current field (w of plans[i]) through steps
+// [j0[i], j1[i]) in one cooperative launch of max(j1 - j0) batched steps.
+// descs: host array already filled by fill_args (snapshots, windows set).
+template <typename C>
+int launch_batched(pe3d_plan_s* owner, std::vector<MarchArgs<C>>& descs, int nsteps, cudaStream_t stream,
+                   void** devbuf, size_t* devbuf_bytes, int* status) {
+    const int n = (int)descs.size();
+    if (n < 1 || n > BATCH_MAX) return fail(PE3D_ERR_ARG, "a batch holds 1 to 64 marches");
+    std::vector<int> pref(2 * (n + 1), 0);
+    int ca = 0, cb = 0;
+    size_t smem = 0;
+    for (int i = 0; i < n; ++i) {
+        const MarchArgs<C>& A = descs[i];
+        pref[i + 1] = pref[i] + (A.Nt + A.NG - 1) / A.NG;
+        pref[n + 1 + i + 1] = pref[n + 1 + i] + A.tiles;
+        ca = std::max(ca, batch_class(A.L));
+        cb = std::max(cb, batch_class(A.Lt));
+        smem = std::max(smem, std::max(smemA_bytes<C>(A.NG, A.ldz, A.T), smemB_bytes<C>(A.rowsB, A.TZ, A.NtP)));
+    }
+    const size_t dbytes = sizeof(MarchArgs<C>) * n;
+    const size_t need = dbytes + sizeof(int) * pref.size();
+    if (need > *devbuf_bytes) {
+        dev_free(owner, devbuf, *devbuf_bytes);
+        *devbuf_bytes = 0;
+        int rc = dev_alloc(owner, devbuf, need);
+        if (rc) return rc;
+        *devbuf_bytes = need;
+    }
+    unsigned char* b = static_cast<unsigned char*>(*devbuf);
+    PE3D_CUDA(cudaMemcpyAsync(b, descs.data(), dbytes, cudaMemcpyHostToDevice, stream));
+    PE3D_CUDA(cudaMemcpyAsync(b + dbytes, pref.data(), sizeof(int) * pref.size(), cudaMemcpyHostToDevice, stream));
+    const void* fn = batch_kernels<C>().k[ca][cb];
+    int nb = 0;
+    PE3D_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, NT, smem));
+    if (nb < 1) return fail(PE3D_ERR_ARG, "batched kernel does not fit on an SM");
+    const int grid = std::min(nb * owner->num_sms, std::max(pref[n], pref[2 * n + 1]));
+    PE3D_CUDA(cudaMemsetAsync(owner->bar, 0, sizeof(unsigned), stream));
+    const MarchArgs<C>* dd = reinterpret_cast<const MarchArgs<C>*>(b);
+    const int* dp = reinterpret_cast<const int*>(b + dbytes);
+    unsigned* bar = owner->bar;
+    int nn = n, ns = nsteps;
+    void* args[] = {&dd, &nn, &dp, &ns, &bar, &status};
+    PE3D_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(NT), args, smem, stream));
+    owner->last_grid = grid;
+    return PE3D_OK;
+}
+
+template <typename C>
+int batched_impl(int n, pe3d_plan_s* const* plans, const void* const* u0, const double* r0, const int* steps,
+                 const int* stride, void* const* out) {
+    pe3d_plan_s* owner = plans[0];
+    for (int i = 1; i < n; ++i)
+        if (plans[i]->stream != owner->stream) return fail(PE3D_ERR_ARG, "batched plans must share one stream");
+    int rc = prepare_kernels<C>(owner);
+    if (rc) return rc;
+    for (int i = 0; i < n; ++i) PE3D_CUDA(cudaMemsetAsync(plans[i]->status, 0, sizeof(int), owner->stream));
+    std::vector<MarchArgs<C>> descs(n);
+    int nsteps = 0;
+    for (int i = 0; i < n; ++i) {
+        pe3d_plan_s* p = plans[i];
+        if (steps[i] > 0 && (rc = step_setup<C>(p, r0[i], steps[i]))) return rc;
+        if ((rc = launch_prologue<C>(p, u0[i], r0[i]))) return rc;
+        fill_args<C>(p, descs[i]);
+        descs[i].snap = reinterpret_cast<C*>(out[i]);
+        descs[i].snap_ld = p->Nz;
+        descs[i].stride = stride[i];
+        descs[i].j0 = 0;
+        descs[i].j1 = steps[i];
+        descs[i].status = owner->status;     // march-time errors are reported through the first plan
+        nsteps = std::max(nsteps, steps[i]);
+        p->last_exec = PE3D_EXEC_PERSISTENT;
+    }
+    if (nsteps == 0) return PE3D_OK;
+    if (owner->timing) PE3D_CUDA(cudaEventRecord(owner->ev0, owner->stream));
+    rc = launch_batched<C>(owner, descs, nsteps, owner->stream, &owner->batchbuf, &owner->batchbuf_bytes,
+                           owner->status);
+    if (rc) return rc;
+    if (owner->timing) PE3D_CUDA(cudaEventRecord(owner->ev1, owner->stream));
+    owner->last_launches = 1 + 2 * n;
+    owner->total_launches += owner->last_launches + n;
+    return PE3D_OK;
+}
+
+}  // namespace pe3d_host

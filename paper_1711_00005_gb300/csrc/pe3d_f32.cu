@@ -7,10 +7,6 @@ int setupA_f32(pe3d_plan_s* p) { return setupA<float2>(p); }
 int march_f32(pe3d_plan_s* p, const void* u0, double r0, int steps, int stride, void* snap, int snap_ld) {
     return march<float2>(p, u0, r0, steps, stride, snap, snap_ld);
 }
-int batched_f32(int n, pe3d_plan_s* const* plans, const void* const* u0, const double* r0, const int* steps,
-                const int* stride, void* const* out) {
-    return batched<float2>(n, plans, u0, r0, steps, stride, out);
-}
 int static_kernels_f32(StaticKernels* k) {
     int rc = prepare_kernels<float2>(nullptr);
     if (rc) return rc;

@@ -55,6 +55,8 @@ struct pe3d_plan_s {
     void* sc = nullptr;               // StepConst [steps]
     int* slice_of_step = nullptr;     // [steps]
     int step_cap = 0;
+    void* batchbuf = nullptr;         // batch descriptors (when this plan leads a batch)
+    size_t batchbuf_bytes = 0;
     int* status = nullptr;            // device status word
     unsigned* bar = nullptr;          // grid-barrier counter
     bool medium_ready = false;

@@ -414,6 +414,57 @@ __global__ void __launch_bounds__(NT) k_march_persistent(const __grid_constant__
     }
 }
 
+// ---------------------------------------------------------------------------
+// batched march: many independent marches of unequal (Nz, Ntheta) advance in
+// the same launches.  Each step's units (phase A: groups of depth systems,
+// phase B: azimuth tiles) of all marches form one list; D[i].j0/j1 give march
+// i its own step window, so marches that started at different times (the
+// request loop) share a launch.  Two grid barriers per step, as above.
+// ---------------------------------------------------------------------------
+constexpr int BATCH_MAX = 64;
+
+__device__ __forceinline__ int find_march(const int* pref, int n, int u) {
+    int lo = 0, hi = n - 1;               // largest i with pref[i] <= u
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pref[mid] <= u) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename C, int LA, int LB>
+__global__ void __launch_bounds__(NT) k_march_batched(const MarchArgs<C>* __restrict__ D, int n,
+                                                      const int* __restrict__ pref, int nsteps, unsigned* bar,
+                                                      int* status) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int s_pa[BATCH_MAX + 1], s_pb[BATCH_MAX + 1], s_j0[BATCH_MAX], s_j1[BATCH_MAX];
+    for (int i = threadIdx.x; i <= n; i += NT) { s_pa[i] = pref[i]; s_pb[i] = pref[n + 1 + i]; }
+    for (int i = threadIdx.x; i < n; i += NT) { s_j0[i] = D[i].j0; s_j1[i] = D[i].j1; }
+    if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t*>(smem), 1);
+    __syncthreads();
+    uint32_t parity = 0;
+    const unsigned G = gridDim.x;
+    unsigned nb = 0;
+    for (int t = 0; t < nsteps; ++t) {
+        for (int u = blockIdx.x; u < s_pa[n]; u += G) {
+            const int i = find_march(s_pa, n, u);
+            const int j = s_j0[i] + t;
+            if (j >= s_j1[i]) continue;
+            if (!phaseA<C, LA>(D[i], j, (u - s_pa[i]) * D[i].NG, smem, parity)) return;
+            __syncthreads();
+        }
+        if (!grid_barrier(bar, (++nb) * G, status)) return;
+        for (int u = blockIdx.x; u < s_pb[n]; u += G) {
+            const int i = find_march(s_pb, n, u);
+            const int j = s_j0[i] + t;
+            if (j >= s_j1[i]) continue;
+            if (!phaseB<C, LB>(D[i], j, u - s_pb[i], smem, parity)) return;
+            __syncthreads();
+        }
+        if (!grid_barrier(bar, (++nb) * G, status)) return;
+    }
+}
+
 // w^0 = [1 + q0 Y] u0 from the caller's [Nt][Nz] field into [Nt][ldz]
 template <typename C>
 __global__ void k_prologue(const C* __restrict__ u0, int Nz, int Nt, int ldz, int periodic,

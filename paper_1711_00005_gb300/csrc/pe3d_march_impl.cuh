@@ -303,14 +303,4 @@ int march(pe3d_plan_s* p, const void* u0_dev, double r0, int steps, int stride, 
     return PE3D_OK;
 }
 
-// ---------------------------------------------------------------------------
-// batched march: every launch advances all unfinished plans by one step
-// ---------------------------------------------------------------------------
-template <typename C>
-int batched(int n, pe3d_plan_s* const* plans, const void* const* u0, const double* r0, const int* steps,
-            const int* stride, void* const* out) {
-    (void)n; (void)plans; (void)u0; (void)r0; (void)steps; (void)stride; (void)out;
-    return fail(PE3D_ERR_STATE, "batched march not built yet");
-}
-
 }  // namespace pe3d_host
