@@ -331,3 +331,19 @@ class Plan:
 
     def __exit__(self, *a):
         self.close()
+
+
+def make_request(grid, n2, slice_r, u0, *, fp32=False, r0=None, steps=None, out_stride=None, rc_every=0):
+    """A pe3d_request over host arrays (the arrays must outlive pe3d_submit,
+    which copies them); returns (request, keepalive)."""
+    n2a = np.ascontiguousarray(n2, dtype=np.complex128)
+    sra = np.ascontiguousarray(slice_r, dtype=np.float64)
+    u0a = np.ascontiguousarray(u0, dtype=np.complex64 if fp32 else np.complex128)
+    steps = grid.steps if steps is None else steps
+    req = pe3d_request(Nz=grid.Nz, Ntheta=grid.Ntheta, dz=grid.dz, dtheta=grid.dtheta, dr=grid.dr, k0=grid.k0,
+                       boundary=PE3D_PERIODIC if grid.periodic else PE3D_WALLED,
+                       precision=PE3D_FP32 if fp32 else PE3D_FP64, rc_every=rc_every,
+                       n2=n2a.ctypes.data, slice_r=sra.ctypes.data, K=len(sra), u0=u0a.ctypes.data,
+                       r0=grid.r0 if r0 is None else r0, steps=steps,
+                       out_stride=(grid.stride if out_stride is None else out_stride))
+    return req, (n2a, sra, u0a)

@@ -6,4 +6,11 @@ int batched_f32(int n, pe3d_plan_s* const* plans, const void* const* u0, const d
                 const int* stride, void* const* out) {
     return batched_impl<float2>(n, plans, u0, r0, steps, stride, out);
 }
+int serve_begin_f32(pe3d_plan_s* p, const void* u0_dev, double r0, int steps, int stride, void* snap_dev,
+                   pe3d::MarchArgs<float2>* desc) {
+    return serve_begin<float2>(p, u0_dev, r0, steps, stride, snap_dev, desc);
+}
+int serve_tick_f32(pe3d_plan_s* owner, pe3d::MarchArgs<float2>* descs, int n, int nsteps) {
+    return serve_tick<float2>(owner, descs, n, nsteps);
+}
 }  // namespace pe3d_host

@@ -120,4 +120,32 @@ int batched_impl(int n, pe3d_plan_s* const* plans, const void* const* u0, const 
     return PE3D_OK;
 }
 
+// Request loop support.  serve_begin prepares one march to be advanced in
+// windows (per-step azimuth setup for all its steps, the prologue from a
+// device u0, its descriptor); serve_tick advances a set of prepared marches
+// through the windows [desc.j0, desc.j1) in one batched launch.
+template <typename C>
+int serve_begin(pe3d_plan_s* p, const void* u0_dev, double r0, int steps, int stride, void* snap_dev,
+                MarchArgs<C>* desc) {
+    int rc;
+    if (steps > 0 && (rc = step_setup<C>(p, r0, steps))) return rc;
+    if ((rc = launch_prologue<C>(p, u0_dev, r0))) return rc;
+    fill_args<C>(p, *desc);
+    desc->snap = reinterpret_cast<C*>(snap_dev);
+    desc->snap_ld = p->Nz;
+    desc->stride = stride;
+    desc->j0 = 0;
+    desc->j1 = 0;
+    p->total_launches += 2;
+    return PE3D_OK;
+}
+
+template <typename C>
+int serve_tick(pe3d_plan_s* owner, MarchArgs<C>* descs, int n, int nsteps) {
+    std::vector<MarchArgs<C>> v(descs, descs + n);
+    for (auto& d : v) d.status = owner->status;
+    return launch_batched<C>(owner, v, nsteps, owner->stream, &owner->batchbuf, &owner->batchbuf_bytes,
+                             owner->status);
+}
+
 }  // namespace pe3d_host
