@@ -343,7 +343,7 @@ int pe3d_destroy(pe3d_plan_t p) {
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
     if (p->capture) cudaStreamDestroy(p->capture);
-    void** bufs[] = {&p->w, &p->v, &p->u0stage, &p->outstage, &p->n2, &p->mz, &p->mB, &p->zsm, &p->batchbuf,
+    void** bufs[] = {&p->w, &p->v, &p->u0stage, &p->outstage, &p->n2, &p->mz, &p->mB, &p->zsm, &p->batchbuf, &p->rc_up, &p->rc_ut, &p->rc_db,
                      &p->gscr, &p->sc, (void**)&p->slice_of_step, (void**)&p->status, (void**)&p->bar};
     for (void** b : bufs)
         if (*b) { cudaFree(*b); *b = nullptr; }

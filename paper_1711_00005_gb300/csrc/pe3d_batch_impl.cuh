@@ -90,6 +90,9 @@ int batched_impl(int n, pe3d_plan_s* const* plans, const void* const* u0, const 
     pe3d_plan_s* owner = plans[0];
     for (int i = 1; i < n; ++i)
         if (plans[i]->stream != owner->stream) return fail(PE3D_ERR_ARG, "batched plans must share one stream");
+    for (int i = 0; i < n; ++i)
+        if (plans[i]->rc_every > 0)
+            return fail(PE3D_ERR_ARG, "the FP64 residual correction runs in single-plan marches only");
     int rc = prepare_kernels<C>(owner);
     if (rc) return rc;
     for (int i = 0; i < n; ++i) PE3D_CUDA(cudaMemsetAsync(plans[i]->status, 0, sizeof(int), owner->stream));

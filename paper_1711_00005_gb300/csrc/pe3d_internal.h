@@ -55,6 +55,9 @@ struct pe3d_plan_s {
     void* sc = nullptr;               // StepConst [steps]
     int* slice_of_step = nullptr;     // [steps]
     int step_cap = 0;
+    void* rc_up = nullptr;            // FP64 residual correction buffers [Nt][ldz]
+    void* rc_ut = nullptr;
+    void* rc_db = nullptr;
     void* batchbuf = nullptr;         // batch descriptors (when this plan leads a batch)
     size_t batchbuf_bytes = 0;
     int* status = nullptr;            // device status word

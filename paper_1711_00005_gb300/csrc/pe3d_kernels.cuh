@@ -55,6 +55,13 @@ struct MarchArgs {
     unsigned* bar;              // grid-barrier counter (persistent launch)
     int* status;
     int j0, j1;                 // steps [j0, j1)
+    // FP64 residual correction every rc_every steps (0: off)
+    int rc_every = 0;
+    const double2* n2 = nullptr;  // complex128 [slices][Nt][Nz] (natural layout)
+    C* up = nullptr;              // u^j before a corrected step      [Nt][ldz]
+    C* ut = nullptr;              // uncorrected u^{j+1}               [Nt][ldz]
+    C* db = nullptr;              // correction d                      [Nt][ldz]
+    double k0 = 0, dz = 0, dr = 0, dtheta = 0, r0 = 0;
 };
 
 __host__ __device__ constexpr size_t align128(size_t x) { return (x + 127) & ~size_t(127); }
@@ -192,7 +199,8 @@ __device__ bool phaseA(const MarchArgs<C>& P, int j, int base, unsigned char* sm
 // (g, k) owns rows k*Lt .. k*Lt+Lt-1 of depth p0+g (Lt <= LB).
 // ---------------------------------------------------------------------------
 template <typename C, int LB>
-__device__ bool phaseB(const MarchArgs<C>& P, int j, int tile, unsigned char* smem, uint32_t& parity) {
+__device__ bool phaseB(const MarchArgs<C>& P, const CUtensorMap* tmap, int j, int tile, unsigned char* smem,
+                       uint32_t& parity, bool solve_only = false) {
     using R = typename real_of<C>::type;
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem);
     const int tid = threadIdx.x;
@@ -217,7 +225,7 @@ __device__ bool phaseB(const MarchArgs<C>& P, int j, int tile, unsigned char* sm
         mbar_arrive_expect_tx(mbar, P.nload * boxb + rowb * (P.periodic ? 2u : 1u));
         const int x = p0 * (int)(sizeof(C) / 8);
         for (int q = 0; q < P.nload; ++q)
-            tma_g2s_2d(tl + (size_t)q * P.BY * TZ, &P.tmap_v, x, q * P.BY, mbar);
+            tma_g2s_2d(tl + (size_t)q * P.BY * TZ, tmap, x, q * P.BY, mbar);
         bulk_g2s(const_cast<C*>(smu), P.mB + (size_t)j * NtP, rowb, mbar);
         if (P.periodic) bulk_g2s(const_cast<C*>(sz), P.zsm + (size_t)j * NtP, rowb, mbar);
     }
@@ -299,8 +307,14 @@ __device__ bool phaseB(const MarchArgs<C>& P, int j, int tile, unsigned char* sm
         if (i < Lt) tk[i * TZ] = vq[i];
     __syncthreads();
     PE3D_MARK(14);
-    const C q = from64<C>(sc.qnext);
-    const bool snap = P.snap != nullptr && ((j + 1) % P.stride) == 0;
+    // On a step that the FP64 correction will redo, keep the uncorrected
+    // field (ut) and let the correction store w, the snapshot and up; before
+    // such a step, keep u^{j+1} (up).  A solve-only pass (the correction's
+    // azimuth solve) stores the solution itself into P.w.
+    const bool refine_now = !solve_only && P.rc_every > 0 && (j + 1) % P.rc_every == 0;
+    const bool refine_next = !solve_only && P.rc_every > 0 && (j + 2) % P.rc_every == 0;
+    const C q = solve_only ? zero : from64<C>(sc.qnext);
+    const bool snap = !solve_only && !refine_now && P.snap != nullptr && ((j + 1) % P.stride) == 0;
     C* sp = snap ? P.snap + (size_t)((j + 1) / P.stride - 1) * Nt * P.snap_ld + p0 + g : nullptr;
     const bool col_ok = p0 + g < P.Nz;
     // neighbours across the chunk edges: row r0-1 and row r0+Lt; the row after
@@ -311,7 +325,9 @@ __device__ bool phaseB(const MarchArgs<C>& P, int j, int tile, unsigned char* sm
     const int rend = min(r0 + Lt, P.rowsB - 1);
     const C up = tl[(size_t)rend * TZ + g];
     const C two = cmake((R)2, (R)0);
-    C* wcol = P.w + (size_t)r0 * ldz + p0 + g;
+    C* wcol = (refine_now ? P.ut : P.w) + (size_t)r0 * ldz + p0 + g;
+    // (a corrected step's own correction stores up, after its residual has read u^j)
+    C* ucol = (refine_next && !refine_now) ? P.up + (size_t)r0 * ldz + p0 + g : nullptr;
 #pragma unroll
     for (int i = 0; i < LB; ++i) {
         const int row = r0 + i;
@@ -319,10 +335,11 @@ __device__ bool phaseB(const MarchArgs<C>& P, int j, int tile, unsigned char* sm
         const C nx2 = (i + 1 == Lt && row + 1 != Nt) ? up : nxt;
         const C prv = (i == 0) ? dn : vq[(i + LB - 1) % LB];
         const C lap = csub(cadd(nx2, prv), cmul(two, vq[i]));
-        const C wn = cfma(q, lap, vq[i]);
+        const C wn = refine_now ? vq[i] : cfma(q, lap, vq[i]);
         if (i < Lt && row < Nt) {
             __stcg(wcol + (size_t)i * ldz, wn);
             if (snap && col_ok) sp[(size_t)row * P.snap_ld] = vq[i];
+            if (ucol) __stcg(ucol + (size_t)i * ldz, vq[i]);
         }
     }
     PE3D_MARK(15);
@@ -347,7 +364,7 @@ __global__ void __launch_bounds__(NT) k_phaseB(const __grid_constant__ MarchArgs
     if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t*>(smem), 1);
     __syncthreads();
     uint32_t parity = 0;
-    phaseB<C, LB>(P, j, blockIdx.x, smem, parity);
+    phaseB<C, LB>(P, &P.tmap_v, j, blockIdx.x, smem, parity);
 }
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -386,7 +403,105 @@ __device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target, int
     return s_ok != 0;
 }
 
-// The whole march in one cooperative launch: two grid barriers per step.
+// ---------------------------------------------------------------------------
+// FP64 residual correction of step j (every rc_every steps):
+//   r = [1 + beta X][1 + (d/4) Y] u^j - [1 + alpha X][1 - (d/4) Y] u~^{j+1}
+// in FP64 from the complex128 medium, d = (A B)^-1 r by the FP32 two-step
+// solve, u^{j+1} = u~^{j+1} + d added in FP64.
+// ---------------------------------------------------------------------------
+template <typename C>
+__device__ __forceinline__ double2 ld64(const C* p) { return to64(__ldcg(p)); }
+
+// [1 + f (d/4) Y] u at (m, l) in FP64, f = +1 (B') or -1 (B)
+template <typename C>
+__device__ double2 theta_apply64(const MarchArgs<C>& P, const C* u, int m, int l, double2 yq) {
+    const int Nt = P.Nt;
+    const size_t ld = P.ldz;
+    const double2 c = ld64(u + (size_t)m * ld + l);
+    double2 up = make_double2(0.0, 0.0), dn = make_double2(0.0, 0.0);
+    if (m + 1 < Nt) up = ld64(u + (size_t)(m + 1) * ld + l); else if (P.periodic) up = ld64(u + l);
+    if (m > 0) dn = ld64(u + (size_t)(m - 1) * ld + l); else if (P.periodic) dn = ld64(u + (size_t)(Nt - 1) * ld + l);
+    const double2 lap = make_double2(up.x + dn.x - 2.0 * c.x, up.y + dn.y - 2.0 * c.y);
+    return cadd(c, cmul(yq, lap));
+}
+
+template <typename C>
+__device__ void residual_phase(const MarchArgs<C>& P, int j) {
+    const double kd = P.k0 * P.dr;
+    const double s = 1.0 / ((P.k0 * P.dz) * (P.k0 * P.dz));
+    const double rs = P.r0 + (double)(j + 1) * P.dr;
+    const double c = 1.0 / ((P.k0 * rs * P.dtheta) * (P.k0 * rs * P.dtheta));
+    const double2 yq = make_double2(0.0, kd * c / 4.0);          // (d/4) c
+    const double2 myq = make_double2(0.0, -kd * c / 4.0);
+    const double2 alpha = make_double2(0.25, -kd / 4.0);
+    const double2 beta = make_double2(0.25, kd / 4.0);
+    const double2* n2 = P.n2 + (size_t)P.slice_of_step[j] * P.Nt * P.Nz;
+    const long long n = (long long)P.Nt * P.ldz;
+    for (long long idx = (long long)blockIdx.x * NT + threadIdx.x; idx < n; idx += (long long)gridDim.x * NT) {
+        const int m = (int)(idx / P.ldz), l = (int)(idx - (long long)m * P.ldz);
+        double2 r = make_double2(0.0, 0.0);
+        if (l < P.Nz) {
+            double2 t1[3], t2[3];
+#pragma unroll
+            for (int d = -1; d <= 1; ++d) {
+                const int ll = l + d;
+                if (ll >= 0 && ll < P.Nz) {
+                    t1[d + 1] = theta_apply64(P, P.up, m, ll, yq);
+                    t2[d + 1] = theta_apply64(P, P.ut, m, ll, myq);
+                } else {
+                    t1[d + 1] = make_double2(0.0, 0.0);
+                    t2[d + 1] = make_double2(0.0, 0.0);
+                }
+            }
+            double2 q = n2[(size_t)m * P.Nz + l];
+            q.x -= 1.0;
+            const double2 x1 = cadd(cmul(q, t1[1]),
+                                    make_double2(s * (t1[2].x + t1[0].x - 2.0 * t1[1].x),
+                                                 s * (t1[2].y + t1[0].y - 2.0 * t1[1].y)));
+            const double2 x2 = cadd(cmul(q, t2[1]),
+                                    make_double2(s * (t2[2].x + t2[0].x - 2.0 * t2[1].x),
+                                                 s * (t2[2].y + t2[0].y - 2.0 * t2[1].y)));
+            r = csub(cadd(t1[1], cmul(beta, x1)), cadd(t2[1], cmul(alpha, x2)));
+        }
+        __stcg(P.v + idx, from64<C>(r));
+    }
+}
+
+// u^{j+1} = u~ + d (FP64 add), then the next step's azimuth stencil, the
+// snapshot and, when the next step is corrected too, up
+template <typename C>
+__device__ void combine_phase(const MarchArgs<C>& P, int j) {
+    using R = typename real_of<C>::type;
+    const int Nt = P.Nt;
+    const size_t ld = P.ldz;
+    const C q = from64<C>(P.sc[j].qnext);
+    const bool snap = P.snap != nullptr && ((j + 1) % P.stride) == 0;
+    C* sp = snap ? P.snap + (size_t)((j + 1) / P.stride - 1) * Nt * P.snap_ld : nullptr;
+    const bool keep = P.rc_every > 0 && (j + 2) % P.rc_every == 0;
+    const C two = cmake((R)2, (R)0);
+    const long long n = (long long)Nt * ld;
+    for (long long idx = (long long)blockIdx.x * NT + threadIdx.x; idx < n; idx += (long long)gridDim.x * NT) {
+        const int m = (int)(idx / ld), l = (int)(idx - (long long)m * ld);
+        auto corrected = [&](int mm) -> C {
+            const size_t o = (size_t)mm * ld + l;
+            return from64<C>(cadd(ld64(P.ut + o), ld64(P.db + o)));
+        };
+        C w = czero<C>(), u = czero<C>();
+        if (l < P.Nz) {
+            u = corrected(m);
+            C upv = czero<C>(), dnv = czero<C>();
+            if (m + 1 < Nt) upv = corrected(m + 1); else if (P.periodic) upv = corrected(0);
+            if (m > 0) dnv = corrected(m - 1); else if (P.periodic) dnv = corrected(Nt - 1);
+            w = cfma(q, csub(cadd(upv, dnv), cmul(two, u)), u);
+            if (snap) sp[(size_t)m * P.snap_ld + l] = u;
+            if (keep) __stcg(P.up + idx, u);
+        }
+        __stcg(P.w + idx, w);
+    }
+}
+
+// The whole march in one cooperative launch: two grid barriers per step (six
+// on a corrected step).
 template <typename C, int LA, int LB>
 __global__ void __launch_bounds__(NT) k_march_persistent(const __grid_constant__ MarchArgs<C> P) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -405,12 +520,39 @@ __global__ void __launch_bounds__(NT) k_march_persistent(const __grid_constant__
         if (!grid_barrier(P.bar, (++nb) * G, P.status)) return;
         PE3D_MARK(17);
         for (int t = blockIdx.x; t < P.tiles; t += G) {
-            if (!phaseB<C, LB>(P, j, t, smem, parity)) return;
+            if (!phaseB<C, LB>(P, &P.tmap_v, j, t, smem, parity)) return;
             __syncthreads();
         }
         PE3D_MARK(18);
         if (!grid_barrier(P.bar, (++nb) * G, P.status)) return;
         PE3D_MARK(19);
+        if (P.rc_every > 0 && (j + 1) % P.rc_every == 0) {
+            residual_phase(P, j);                                   // r into v
+            if (!grid_barrier(P.bar, (++nb) * G, P.status)) return;
+            MarchArgs<C> Q = P;                                    // A^-1 r into v
+            Q.w = P.v;
+            Q.c1 = czero<C>();
+            Q.c2p = from64<C>(make_double2(0.0, 0.0));
+            {
+                const double s = 1.0 / ((P.k0 * P.dz) * (P.k0 * P.dz));
+                const double2 e = make_double2(0.25 * s, -P.k0 * P.dr / 4.0 * s);
+                const double en = e.x * e.x + e.y * e.y;
+                Q.c2p = from64<C>(make_double2(-e.x / en, e.y / en));   // -1/e
+            }
+            for (int u = blockIdx.x; u < unitsA; u += G) {
+                if (!phaseA<C, LA>(Q, j, u * P.NG, smem, parity)) return;
+                __syncthreads();
+            }
+            if (!grid_barrier(P.bar, (++nb) * G, P.status)) return;
+            Q.w = P.db;                                            // B^-1 A^-1 r into db
+            for (int t = blockIdx.x; t < P.tiles; t += G) {
+                if (!phaseB<C, LB>(Q, &P.tmap_v, j, t, smem, parity, true)) return;
+                __syncthreads();
+            }
+            if (!grid_barrier(P.bar, (++nb) * G, P.status)) return;
+            combine_phase(P, j);
+            if (!grid_barrier(P.bar, (++nb) * G, P.status)) return;
+        }
     }
 }
 
@@ -458,7 +600,7 @@ __global__ void __launch_bounds__(NT) k_march_batched(const MarchArgs<C>* __rest
             const int i = find_march(s_pb, n, u);
             const int j = s_j0[i] + t;
             if (j >= s_j1[i]) continue;
-            if (!phaseB<C, LB>(D[i], j, u - s_pb[i], smem, parity)) return;
+            if (!phaseB<C, LB>(D[i], &D[i].tmap_v, j, u - s_pb[i], smem, parity)) return;
             __syncthreads();
         }
         if (!grid_barrier(bar, (++nb) * G, status)) return;

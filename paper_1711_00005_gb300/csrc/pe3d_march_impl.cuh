@@ -132,6 +132,12 @@ void fill_args(pe3d_plan_s* p, MarchArgs<C>& A) {
     A.snap = nullptr; A.snap_ld = p->Nz; A.stride = 1;
     A.bar = p->bar; A.status = p->status;
     A.j0 = 0; A.j1 = 0;
+    A.rc_every = 0;
+    A.n2 = reinterpret_cast<const double2*>(p->n2);
+    A.up = reinterpret_cast<C*>(p->rc_up);
+    A.ut = reinterpret_cast<C*>(p->rc_ut);
+    A.db = reinterpret_cast<C*>(p->rc_db);
+    A.k0 = p->k0; A.dz = p->dz; A.dr = p->dr; A.dtheta = p->dtheta; A.r0 = 0;
 }
 
 // every compiled (depth chunk, azimuth chunk) specialisation
@@ -296,6 +302,26 @@ int march(pe3d_plan_s* p, const void* u0_dev, double r0, int steps, int stride, 
     A.snap = reinterpret_cast<C*>(snap_dev);
     A.snap_ld = snap_ld;
     A.stride = stride;
+    A.r0 = r0;
+    if (p->rc_every > 0 && steps > 0) {
+        // FP64 residual correction: persistent launch only; buffers on first use
+        if (p->exec != PE3D_EXEC_AUTO && p->exec != PE3D_EXEC_PERSISTENT)
+            return fail(PE3D_ERR_ARG, "the FP64 residual correction runs in the persistent launch only");
+        const size_t fb = (size_t)p->Nt * p->ldz * sizeof(C);
+        void** bufs[3] = {&p->rc_up, &p->rc_ut, &p->rc_db};
+        for (void** b : bufs)
+            if (!*b) {
+                if ((rc = dev_alloc(p, b, fb))) return rc;
+                PE3D_CUDA(cudaMemsetAsync(*b, 0, fb, p->stream));
+            }
+        A.up = reinterpret_cast<C*>(p->rc_up);
+        A.ut = reinterpret_cast<C*>(p->rc_ut);
+        A.db = reinterpret_cast<C*>(p->rc_db);
+        A.rc_every = p->rc_every;
+        if (p->rc_every == 1)   // step 0 is corrected: its u^j is u0
+            PE3D_CUDA(cudaMemcpy2DAsync(p->rc_up, p->ldz * sizeof(C), u0_dev, p->Nz * sizeof(C),
+                                        p->Nz * sizeof(C), p->Nt, cudaMemcpyDeviceToDevice, p->stream));
+    }
     rc = run_steps<C>(p, A, steps);
     if (rc) return rc;
     p->last_launches += 1 + (steps > 0 ? 1 : 0);   // prologue, azimuth setup

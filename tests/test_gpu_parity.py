@@ -249,3 +249,52 @@ def test_batched_matches_single_marches(P, oracle_lib):
             assert relerrs(got, ref).max() < (TOL32 if fp32 else TOL64)
         for pl in plans:
             pl.close()
+
+
+# ---------------------------------------------------------------------------
+# FP64 residual correction (FP32 march)
+# ---------------------------------------------------------------------------
+
+def _march_rc(P, wl, rc, steps=None, stride=None, exec_mode=None):
+    g = wl.grid
+    steps = g.steps if steps is None else steps
+    stride = g.stride if stride is None else stride
+    with P.Plan.for_grid(g, fp32=True, exec_mode=exec_mode) as plan:
+        P.pe3d_set_option(plan.h, P.PE3D_OPT_RC_EVERY, rc)
+        plan.set_medium(torch.from_numpy(wl.n2).cuda(), wl.slice_r)
+        u0 = torch.from_numpy(wl.u0.astype(np.complex64)).cuda()
+        out = plan.march(u0, g.r0, steps, stride)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("periodic", [False, True], ids=["walled", "periodic"])
+def test_residual_correction_every_step(P, oracle_lib, periodic):
+    """Correcting every step in FP64 leaves only the rounding of the stored
+    field: far closer to the FP64 oracle than the plain FP32 march."""
+    wl = workloads.random_case(200, 48, periodic=periodic, K=4, steps=300, seed=400, stride=50,
+                               lossy=True, theta_dependent=True)
+    ref = oracle_lib.march(wl.grid, wl.n2, wl.slice_r, wl.u0)
+    plain = relerrs(_march_rc(P, wl, 0), ref)
+    corr = relerrs(_march_rc(P, wl, 1), ref)
+    print("plain", plain, "corrected", corr)
+    assert corr.max() < 2e-6
+    assert corr.max() < plain.max() / 3
+
+
+@pytest.mark.parametrize("rc", [7, 64])
+def test_residual_correction_periodic_steps(P, oracle_lib, rc):
+    """A correction every rc steps (snapshots landing on corrected and on
+    uncorrected steps) stays within the FP32 tolerance and changes the field."""
+    wl = workloads.random_case(150, 40, periodic=False, K=3, steps=140, seed=401, stride=7)
+    ref = oracle_lib.march(wl.grid, wl.n2, wl.slice_r, wl.u0)
+    got = _march_rc(P, wl, rc)
+    assert relerrs(got, ref).max() < TOL32
+    assert not np.array_equal(got, _march_rc(P, wl, 0))
+
+
+def test_residual_correction_needs_persistent(P):
+    wl = workloads.random_case(20, 6, periodic=False, K=1, steps=4, seed=402)
+    with pytest.raises(P.PE3DError) as e:
+        _march_rc(P, wl, 2, exec_mode=P.PE3D_EXEC_STREAM)
+    assert e.value.code == P.PE3D_ERR_ARG
