@@ -259,6 +259,9 @@ def run_ours(args):
     fp32 = precision == "fp32"
     wl = make()
     g = wl.grid
+    if args.range_steps:                      # a truncated march (profiling cases)
+        g.steps = min(g.steps, args.range_steps)
+        g.stride = max(1, min(g.stride, g.steps))
     point_steps = g.point_steps
     cdt = np.complex64 if fp32 else np.complex128
     tcdt = torch.complex64 if fp32 else torch.complex128
@@ -284,6 +287,8 @@ def run_ours(args):
                        P.PE3D_FP32 if fp32 else P.PE3D_FP64, stream)
     P.pe3d_set_option(plan, P.PE3D_OPT_EXEC, args.exec)
     P.pe3d_set_option(plan, P.PE3D_OPT_TIMING, 1)
+    if args.rc:
+        P.pe3d_set_option(plan, P.PE3D_OPT_RC_EVERY, args.rc)
 
     def step():
         P.pe3d_set_medium(plan, n2_dev, wl.slice_r)
@@ -389,6 +394,7 @@ def run_ours(args):
                 "medium_slices": len(wl.slice_r), "point_steps_per_march": point_steps,
                 "precision": "complex64 march, FP64 coefficient setup" if fp32 else "complex128",
                 "exec": ["auto", "stream", "graph", "persistent"][info["exec"]],
+                "fp64_residual_correction_every": args.rc or None,
                 "layout": {k: info[k] for k in ("ldz", "zthreads", "zchunk", "ttile", "tchunk", "grid")},
                 "l2": "flushed each step: the step re-reads the 441 MB n^2 and rewrites 220 MB of "
                       "coefficients (> 129 MB L2) before the march",
@@ -422,10 +428,14 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--ref-sample-steps", type=int, default=200)
+    ap.add_argument("--range-steps", type=int, default=0, help="truncate the march (profiling)")
+    ap.add_argument("--rc", type=int, default=0, help="FP64 residual correction every K steps (FP32)")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)     # timing rule: at least 3 untimed warm-up steps
     if args.impl == "reference":
         return run_reference(args)
+    if args.rc and WORKLOADS[args.workload][0] != "fp32":
+        ap.error("--rc applies to FP32 workloads")
     return run_ours(args)
 
 
