@@ -107,10 +107,16 @@ int encode_tmap_v(pe3d_plan_s* p) {
     const cuuint64_t strides[1] = {(cuuint64_t)p->ldz * elem_bytes(p)};
     const cuuint32_t box[2] = {(cuuint32_t)(p->TZ * units), (cuuint32_t)p->BY};
     const cuuint32_t estr[2] = {1, 1};
-    CUresult r = encode(&p->tmap_v, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, p->v, dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(PE3D_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    void* bufs[1] = {p->v};
+    CUtensorMap* maps[1] = {&p->tmap_v};
+    for (int i = 0; i < 1; ++i) {
+        if (!bufs[i]) continue;
+        CUresult r = encode(maps[i], CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, bufs[i], dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS)
+            return fail(PE3D_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    }
     return PE3D_OK;
 }
 

@@ -108,6 +108,13 @@ struct ScanGeom {
 
 // Exclusive carry of the scan, evaluated at zero: forward (FWD) returns the
 // composition of chunks 0..k-1 applied to 0, backward that of chunks K-1..k+1.
+// Across warps (W <= 8) each thread loads the aggregates of the warps before
+// it (identity elsewhere) and composes them as a fixed-order tree.  Forward
+// and backward scans use separate halves of the scratch (scr and scr + 8 *
+// sstride), so a scan needs one __syncthreads.
+template <typename C>
+__device__ __forceinline__ Aff<C> aff_id() { Aff<C> r; r.a = cone<C>(); r.b = czero<C>(); return r; }
+
 template <typename C, bool FWD>
 __device__ __forceinline__ C scan_carry(Aff<C> x, const ScanGeom& g, Aff<C>* scr) {
     const int pos = FWD ? g.kw : (g.KW - 1 - g.kw);
@@ -119,14 +126,23 @@ __device__ __forceinline__ C scan_carry(Aff<C> x, const ScanGeom& g, Aff<C>* scr
         else     { o.a = shfl_down(x.a, d * g.S); o.b = shfl_down(x.b, d * g.S); }
         if (pos >= d) x = then(o, x);
     }
-    Aff<C> P; P.a = cone<C>(); P.b = czero<C>();
+    Aff<C> P = aff_id<C>();
     if (g.W > 1) {
+        Aff<C>* buf = FWD ? scr : scr + 8 * g.sstride;
         const bool last = FWD ? (g.kw == g.KW - 1) : (g.kw == 0);
-        if (last) scr[g.wk * g.sstride] = x;
+        if (last) buf[g.wk * g.sstride] = x;
         __syncthreads();
-        if (FWD) { for (int w = 0; w < g.wk; ++w) P = then(P, scr[w * g.sstride]); }
-        else     { for (int w = g.W - 1; w > g.wk; --w) P = then(P, scr[w * g.sstride]); }
-        __syncthreads();
+        Aff<C> e[8];
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            const bool use = FWD ? (w < g.wk) : (w > g.wk && w < g.W);
+            e[w] = use ? buf[w * g.sstride] : aff_id<C>();
+        }
+        if (FWD) {
+            P = then(then(then(e[0], e[1]), then(e[2], e[3])), then(then(e[4], e[5]), then(e[6], e[7])));
+        } else {
+            P = then(then(then(e[7], e[6]), then(e[5], e[4])), then(then(e[3], e[2]), then(e[1], e[0])));
+        }
     }
     const Aff<C> full = then(P, x);
     const C nb = FWD ? shfl_up(full.b, g.S) : shfl_down(full.b, g.S);

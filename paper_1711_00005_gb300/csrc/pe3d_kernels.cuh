@@ -77,7 +77,7 @@ template <typename C>
 __host__ __device__ inline size_t smemA_group(int ldz) { return align128((size_t)2 * ldz * sizeof(C)); }
 template <typename C>
 __host__ __device__ inline size_t smemA_bytes(int NG, int ldz, int T) {
-    return 128 + (size_t)NG * smemA_group<C>(ldz) + align128((size_t)NG * (T / 32) * sizeof(Aff<C>));
+    return 128 + (size_t)NG * smemA_group<C>(ldz) + align128((size_t)NG * 16 * sizeof(Aff<C>));
 }
 template <typename C>
 struct SmemB {
@@ -87,7 +87,7 @@ struct SmemB {
         tile = o; o += align128((size_t)rowsB * TZ * sizeof(C));
         mu = o;   o += align128((size_t)NtP * sizeof(C));
         z = o;    o += align128((size_t)NtP * sizeof(C));
-        scr = o;  o += align128((size_t)TZ * (NT / 32) * sizeof(Aff<C>));
+        scr = o;  o += align128((size_t)TZ * 16 * sizeof(Aff<C>));
         sf = o;   o += align128((size_t)2 * TZ * sizeof(double2));
         total = o;
     }
@@ -111,7 +111,7 @@ __device__ bool phaseA(const MarchArgs<C>& P, int j, int base, unsigned char* sm
     const size_t gstride = smemA_group<C>(ldz);
     C* sw = reinterpret_cast<C*>(smem + 128 + gs * gstride);   // w, overwritten by v
     const C* sm = sw + ldz;
-    Aff<C>* scr = reinterpret_cast<Aff<C>*>(smem + 128 + P.NG * gstride) + gs * (P.T / 32);
+    Aff<C>* scr = reinterpret_cast<Aff<C>*>(smem + 128 + P.NG * gstride) + gs * 16;
 
     // 1. one thread stages every active group's column of w and of the slice's
     //    multipliers with bulk copies (one round trip)
@@ -326,7 +326,6 @@ __device__ bool phaseB(const MarchArgs<C>& P, const CUtensorMap* tmap, int j, in
     const C up = tl[(size_t)rend * TZ + g];
     const C two = cmake((R)2, (R)0);
     C* wcol = (refine_now ? P.ut : P.w) + (size_t)r0 * ldz + p0 + g;
-    // (a corrected step's own correction stores up, after its residual has read u^j)
     C* ucol = (refine_next && !refine_now) ? P.up + (size_t)r0 * ldz + p0 + g : nullptr;
 #pragma unroll
     for (int i = 0; i < LB; ++i) {
@@ -366,6 +365,10 @@ __global__ void __launch_bounds__(NT) k_phaseB(const __grid_constant__ MarchArgs
     uint32_t parity = 0;
     phaseB<C, LB>(P, &P.tmap_v, j, blockIdx.x, smem, parity);
 }
+
+// leave the kernel after a failed bounded wait (no copy of this CTA is in
+// flight then: every wait that can fail follows its own copies' completion)
+#define PE3D_ABORT() return
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     unsigned v;
@@ -513,22 +516,22 @@ __global__ void __launch_bounds__(NT) k_march_persistent(const __grid_constant__
     const int unitsA = (P.Nt + P.NG - 1) / P.NG;
     for (int j = P.j0; j < P.j1; ++j) {
         for (int u = blockIdx.x; u < unitsA; u += G) {
-            if (!phaseA<C, LA>(P, j, u * P.NG, smem, parity)) return;
+            if (!phaseA<C, LA>(P, j, u * P.NG, smem, parity)) PE3D_ABORT();
             __syncthreads();
         }
         PE3D_MARK(16);
-        if (!grid_barrier(P.bar, (++nb) * G, P.status)) return;
+        if (!grid_barrier(P.bar, (++nb) * G, P.status)) PE3D_ABORT();
         PE3D_MARK(17);
         for (int t = blockIdx.x; t < P.tiles; t += G) {
-            if (!phaseB<C, LB>(P, &P.tmap_v, j, t, smem, parity)) return;
+            if (!phaseB<C, LB>(P, &P.tmap_v, j, t, smem, parity)) PE3D_ABORT();
             __syncthreads();
         }
         PE3D_MARK(18);
-        if (!grid_barrier(P.bar, (++nb) * G, P.status)) return;
+        if (!grid_barrier(P.bar, (++nb) * G, P.status)) PE3D_ABORT();
         PE3D_MARK(19);
         if (P.rc_every > 0 && (j + 1) % P.rc_every == 0) {
             residual_phase(P, j);                                   // r into v
-            if (!grid_barrier(P.bar, (++nb) * G, P.status)) return;
+            if (!grid_barrier(P.bar, (++nb) * G, P.status)) PE3D_ABORT();
             MarchArgs<C> Q = P;                                    // A^-1 r into v
             Q.w = P.v;
             Q.c1 = czero<C>();
@@ -540,18 +543,18 @@ __global__ void __launch_bounds__(NT) k_march_persistent(const __grid_constant__
                 Q.c2p = from64<C>(make_double2(-e.x / en, e.y / en));   // -1/e
             }
             for (int u = blockIdx.x; u < unitsA; u += G) {
-                if (!phaseA<C, LA>(Q, j, u * P.NG, smem, parity)) return;
+                if (!phaseA<C, LA>(Q, j, u * P.NG, smem, parity)) PE3D_ABORT();
                 __syncthreads();
             }
-            if (!grid_barrier(P.bar, (++nb) * G, P.status)) return;
+            if (!grid_barrier(P.bar, (++nb) * G, P.status)) PE3D_ABORT();
             Q.w = P.db;                                            // B^-1 A^-1 r into db
             for (int t = blockIdx.x; t < P.tiles; t += G) {
-                if (!phaseB<C, LB>(Q, &P.tmap_v, j, t, smem, parity, true)) return;
+                if (!phaseB<C, LB>(Q, &P.tmap_v, j, t, smem, parity, true)) PE3D_ABORT();
                 __syncthreads();
             }
-            if (!grid_barrier(P.bar, (++nb) * G, P.status)) return;
+            if (!grid_barrier(P.bar, (++nb) * G, P.status)) PE3D_ABORT();
             combine_phase(P, j);
-            if (!grid_barrier(P.bar, (++nb) * G, P.status)) return;
+            if (!grid_barrier(P.bar, (++nb) * G, P.status)) PE3D_ABORT();
         }
     }
 }
@@ -592,18 +595,18 @@ __global__ void __launch_bounds__(NT) k_march_batched(const MarchArgs<C>* __rest
             const int i = find_march(s_pa, n, u);
             const int j = s_j0[i] + t;
             if (j >= s_j1[i]) continue;
-            if (!phaseA<C, LA>(D[i], j, (u - s_pa[i]) * D[i].NG, smem, parity)) return;
+            if (!phaseA<C, LA>(D[i], j, (u - s_pa[i]) * D[i].NG, smem, parity)) PE3D_ABORT();
             __syncthreads();
         }
-        if (!grid_barrier(bar, (++nb) * G, status)) return;
+        if (!grid_barrier(bar, (++nb) * G, status)) PE3D_ABORT();
         for (int u = blockIdx.x; u < s_pb[n]; u += G) {
             const int i = find_march(s_pb, n, u);
             const int j = s_j0[i] + t;
             if (j >= s_j1[i]) continue;
-            if (!phaseB<C, LB>(D[i], &D[i].tmap_v, j, u - s_pb[i], smem, parity)) return;
+            if (!phaseB<C, LB>(D[i], &D[i].tmap_v, j, u - s_pb[i], smem, parity)) PE3D_ABORT();
             __syncthreads();
         }
-        if (!grid_barrier(bar, (++nb) * G, status)) return;
+        if (!grid_barrier(bar, (++nb) * G, status)) PE3D_ABORT();
     }
 }
 
