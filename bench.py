@@ -417,23 +417,239 @@ def run_ours(args):
     return 0
 
 
+def run_batched(args):
+    """32 frequencies, 25-400 Hz, on one 30 deg sector over 3000 m to 20 km, all
+    marched in one batched persistent launch (complex FP32, FP64 setup).  The
+    oracle marches the four lowest frequencies in full for parity and for the
+    CPU baseline."""
+    import torch
+    import oracle
+    from paper_1711_00005_gb300 import build
+    build.build()
+    import paper_1711_00005_gb300 as P
+    grids = workloads.config4_grids()
+    if args.members:                          # the highest-frequency members only (profiling cases)
+        grids = grids[-args.members:]
+    if args.range_steps:
+        for g in grids:
+            g.steps = min(g.steps, args.range_steps)
+    for g in grids:
+        g.stride = g.steps
+    wls = [workloads.config4_member(g) for g in grids]
+    point_steps = sum(g.point_steps for g in grids)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    plans, n2s, u0s, outs = [], [], [], []
+    for wl in wls:
+        g = wl.grid
+        h = P.pe3d_plan(g.Nz, g.Ntheta, g.dz, g.dtheta, g.dr, g.k0, P.PE3D_WALLED, P.PE3D_FP32, stream)
+        plans.append(h)
+        n2s.append(torch.from_numpy(wl.n2).to(dev))
+        u0s.append(torch.from_numpy(wl.u0.astype(np.complex64)).to(dev))
+        outs.append(torch.empty((1, g.Ntheta, g.Nz), dtype=torch.complex64, device=dev))
+    P.pe3d_set_option(plans[0], P.PE3D_OPT_TIMING, 1)
+    torch.cuda.synchronize()
+
+    def step():
+        for h, n2, wl in zip(plans, n2s, wls):
+            P.pe3d_set_medium(h, n2, wl.slice_r)
+        P.pe3d_march_batched(plans, u0s, [g.r0 for g in grids], [g.steps for g in grids],
+                             [g.stride for g in grids], outs)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # parity and CPU baseline: the four lowest frequencies, full marches
+    cores = oracle.default_threads()
+    err, t_cpu, ps_cpu = 0.0, 0.0, 0
+    if not args.no_cpu_baseline:
+        for i in range(min(4, len(wls))):
+            ref, dt = oracle_run(wls[i], grids[i].steps, cores)
+            got = outs[i].cpu().numpy()
+            err = max(err, max(relerr_series(got, ref)))
+            t_cpu += dt
+            ps_cpu += grids[i].point_steps
+    sampler = ClockSampler(gpu_uuid())
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    kernel_ns = []
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+        kernel_ns.append(P.pe3d_plan_info(plans[0])["kernel_ns"])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    t = ev0.elapsed_time(ev1) / 1e3
+    peak, peak_kind = measured_peaks()
+    kns = statistics.mean(kernel_ns) if kernel_ns and kernel_ns[0] > 0 else None
+    roof = None
+    if kns:
+        achieved = 40 * point_steps / (kns * 1e-9) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": f"{peak_kind} hbm_gbs", "kernel": "k_march_batched<float2>",
+                "algorithmic_bytes_per_launch": 40 * point_steps, "kernel_ms": kns / 1e6,
+                "traffic": recorded_traffic("k_march_batched<float2>", "batched-32f-25-400Hz")}
+    # end to end: host (pinned) media and starters through the same calls
+    n2h = [torch.from_numpy(wl.n2).pin_memory() for wl in wls]
+    u0h = [torch.from_numpy(wl.u0.astype(np.complex64)).pin_memory() for wl in wls]
+    outh = [torch.empty((1, g.Ntheta, g.Nz), dtype=torch.complex64).pin_memory() for g in grids]
+    t0 = time.perf_counter()
+    for h, n2, wl in zip(plans, n2h, wls):
+        P.pe3d_set_medium(h, n2, wl.slice_r)
+    for u, ud in zip(u0h, u0s):
+        ud.copy_(u, non_blocking=True)
+    P.pe3d_march_batched(plans, u0s, [g.r0 for g in grids], [g.steps for g in grids],
+                         [g.stride for g in grids], outs)
+    for o, od in zip(outh, outs):
+        o.copy_(od)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    line = {
+        "metric": METRIC, "value": point_steps * args.steps / t, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batched-32f-25-400Hz", "marches": len(grids), "point_steps_per_launch": point_steps,
+                   "range_steps": [grids[0].steps, grids[-1].steps],
+                   "grid_range": [[grids[0].Nz, grids[0].Ntheta], [grids[-1].Nz, grids[-1].Ntheta]],
+                   "precision": "complex64 march, FP64 coefficient setup", "exec": "one batched persistent launch",
+                   "l2": "working set (fields and coefficients of 32 marches, ~0.6 GB) exceeds the 129 MB L2"},
+        "max_rel_l2_vs_oracle": err if not args.no_cpu_baseline else None,
+        "roofline": roof,
+        "cpu_baseline": None if args.no_cpu_baseline else {
+            "value": ps_cpu / t_cpu, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "full marches of the four lowest frequencies (25-29 Hz), FP64 C oracle"},
+        "e2e": {"value": point_steps / t_e2e, "unit": UNIT,
+                "h2d_bytes_per_step": int(sum(wl.n2.nbytes for wl in wls) + sum(u.numel() * 8 for u in u0h)),
+                "d2h_bytes_per_step": int(sum(o.numel() * 8 for o in outh))},
+        # per step and march: depth setup, azimuth setup, prologue; plus the one batched march
+        "gpu_launches": int(len(plans) * 3 + 1) * args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    for h in plans:
+        P.pe3d_destroy(h)
+    return 0
+
+
+def run_served(args):
+    """The request loop under a Poisson stream (seed 5): f ~ U(25,400) Hz, sector
+    width ~ U(10,360) deg, range ~ U(5,30) km; dz = lambda/8 over 1000 m,
+    dr = lambda/4, Ntheta scaled with the width; one seeded medium slice per
+    request (Munk + perturbations, generated at arrival).  Reports p50/p99
+    submit-to-done latency, offered and served grid-point range-steps/s and the
+    backlog left when the run stops."""
+    import torch
+    from paper_1711_00005_gb300 import build
+    build.build()
+    import paper_1711_00005_gb300 as P
+    reqs = workloads.config5_stream(rate=args.serve_rate, duration=args.serve_duration, seed=5)
+    grids = [workloads.config5_grid(r, max_steps=args.range_steps or None) for r in reqs]
+    offered_ps = sum(g.point_steps for g in grids)
+    srv = P.pe3d_server_create(int(args.serve_budget_gb * (1 << 30)), 64, args.serve_chunk)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(gpu_uuid())
+    t0 = time.perf_counter()
+    pending = {}          # id -> (index, grid, keepalive)
+    done = []             # (index, times)
+    sample = {}           # index -> result (first few, for the alone-vs-mix check)
+    i = 0
+    deadline = args.serve_duration + args.serve_max_wait
+    while True:
+        now = time.perf_counter() - t0
+        while i < len(reqs) and reqs[i].t_arrive <= now:
+            wl = workloads.config5_member(reqs[i], grids[i], n_slices=1)
+            req, keep = P.make_request(grids[i], wl.n2, wl.slice_r, wl.u0, fp32=True,
+                                       out_stride=grids[i].steps)
+            rid = P.pe3d_submit(srv, req)
+            pending[rid] = (i, grids[i], keep, wl)
+            i += 1
+        for rid in list(pending):
+            st, tm = P.pe3d_poll(srv, rid)
+            if st == P.PE3D_REQ_DONE:
+                idx, g, keep, wl = pending.pop(rid)
+                out = np.empty((1, g.Ntheta, g.Nz), np.complex64)
+                P.pe3d_poll(srv, rid, out)
+                done.append((idx, tm))
+                if len(sample) < args.serve_check:
+                    sample[idx] = (wl, out)
+            elif st == P.PE3D_REQ_FAILED:
+                raise RuntimeError(f"request {rid} failed")
+        if i == len(reqs) and not pending:
+            break
+        if now > deadline:
+            break
+        time.sleep(0.001)
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    stats = P.pe3d_server_stats(srv)
+    P.pe3d_server_destroy(srv)
+    lat = sorted(tm[2] - tm[0] for _, tm in done)
+    served_ps = sum(grids[idx].point_steps for idx, _ in done)
+    t_first = min(tm[0] for _, tm in done) if done else 0.0
+    t_last = max(tm[2] for _, tm in done) if done else 1.0
+    # the same requests marched alone (pe3d_march) give bit-identical fields
+    same = True
+    for idx, (wl, out) in sample.items():
+        g = grids[idx]
+        with P.Plan.for_grid(g, fp32=True) as plan:
+            plan.set_medium(wl.n2, wl.slice_r)
+            ref = np.zeros((1, g.Ntheta, g.Nz), np.complex64)
+            P.pe3d_march(plan.h, wl.u0.astype(np.complex64), g.r0, g.steps, g.steps, ref)
+        same = same and bool(np.array_equal(out, ref))
+    pct = lambda q: lat[min(len(lat) - 1, int(q * len(lat)))] if lat else None
+    value = served_ps / (t_last - t_first) if done else 0.0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": len(done), "warmup": 0,
+        "ms_per_step": (t_last - t_first) / max(1, len(done)) * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"served-poisson-{args.serve_rate:g}rps-{args.serve_duration:g}s",
+                   "requests_offered": len(reqs), "requests_done": len(done), "backlog_at_stop": len(pending),
+                   "never_submitted": len(reqs) - i, "offered_point_steps": offered_ps,
+                   "offered_point_steps_per_s": offered_ps / args.serve_duration,
+                   "chunk_steps_per_tick": args.serve_chunk, "max_active": 64,
+                   "precision": "complex64 march, FP64 coefficient setup",
+                   "medium": "one seeded slice per request (Munk + perturbations)"},
+        "latency_s": {"p50": pct(0.50), "p99": pct(0.99), "max": lat[-1] if lat else None},
+        "alone_vs_mix_bitwise": same, "alone_vs_mix_checked": len(sample),
+        "server_stats": stats, "wall_s": wall, "clocks": clocks,
+        "roofline": None, "cpu_baseline": None,
+        "e2e": {"value": value, "unit": UNIT, "note": "host media in, host fields out through pe3d_submit/poll"},
+        "gpu_launches": None,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="medium-100Hz")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched-25-400Hz", "served"], default="medium-100Hz")
     ap.add_argument("--exec", type=int, default=3, help="1 stream, 2 graph, 3 persistent")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--ref-sample-steps", type=int, default=200)
     ap.add_argument("--range-steps", type=int, default=0, help="truncate the march (profiling)")
     ap.add_argument("--rc", type=int, default=0, help="FP64 residual correction every K steps (FP32)")
+    ap.add_argument("--members", type=int, default=0, help="batched workload: highest-frequency members only")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="served workload: Poisson arrivals per s")
+    ap.add_argument("--serve-duration", type=float, default=60.0, help="served workload: seconds of arrivals")
+    ap.add_argument("--serve-max-wait", type=float, default=120.0, help="served workload: stop this long after")
+    ap.add_argument("--serve-chunk", type=int, default=64, help="served workload: range steps per tick")
+    ap.add_argument("--serve-budget-gb", type=float, default=96.0, help="served workload: device memory budget")
+    ap.add_argument("--serve-check", type=int, default=4, help="served workload: results re-marched alone")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)     # timing rule: at least 3 untimed warm-up steps
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched-25-400Hz":
+        return run_batched(args)
+    if args.workload == "served":
+        return run_served(args)
     if args.rc and WORKLOADS[args.workload][0] != "fp32":
         ap.error("--rc applies to FP32 workloads")
     return run_ours(args)

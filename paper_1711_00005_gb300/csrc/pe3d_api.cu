@@ -1,5 +1,6 @@
 // pe3d_api.cu -- the extern "C" boundary: argument checking, plan memory,
 // staging of host buffers, and dispatch to the FP32 / FP64 launch layers.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -339,6 +340,15 @@ int pe3d_march_batched(int n, const pe3d_plan_t* plans, const void* const* u0, c
     if (rc) return rc;
     for (int i = 0; i < n; ++i)
         if ((rc = read_status(plans[i]))) return rc;
+    pe3d_plan_s* owner = plans[0];
+    owner->last_kernel_ns = 0;
+    int nsteps = 0;
+    for (int i = 0; i < n; ++i) nsteps = std::max(nsteps, steps[i]);
+    if (owner->timing && nsteps > 0) {
+        float ms = 0.f;
+        PE3D_CUDA(cudaEventElapsedTime(&ms, owner->ev0, owner->ev1));
+        owner->last_kernel_ns = (int64_t)((double)ms * 1e6);
+    }
     return PE3D_OK;
 }
 

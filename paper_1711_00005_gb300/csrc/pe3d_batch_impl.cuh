@@ -29,7 +29,10 @@ const BatchTable<C>& batch_kernels() {
     if (!attr) {
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b)
+            {
                 cudaFuncSetAttribute(t.k[a][b], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BUDGET);
+                cudaFuncSetAttribute(t.k[a][b], cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+            }
         attr = true;
     }
     return t;

@@ -140,35 +140,52 @@ __device__ bool phaseA(const MarchArgs<C>& P, int j, int base, unsigned char* sm
     // The chunk is held in registers; elements i >= L (only when L < LA) act
     // as the identity map (mu = 1, w = 0), so every pass is branch-free.
     const C one = cone<C>(), zero = czero<C>();
-    C wq[LA], mq[LA], gq[LA];
+    // Short chunks keep w and mu in registers; long chunks (LA >= 17) hold only
+    // the running solution and stream w and mu from shared memory, which keeps
+    // registers low enough for two CTAs per SM on throughput-bound batches.
+    constexpr bool HOLD = LA <= 9;
+    constexpr int LH = HOLD ? LA : 1;
+    C wq[LH], mq[LH], gq[LA];
+    if (HOLD) {
 #pragma unroll
-    for (int i = 0; i < LA; ++i) {
-        const int ii = min(i, L - 1);
-        wq[i] = i < L ? wk_[ii] : zero;
-        mq[i] = i < L ? mk[ii] : one;
+        for (int i = 0; i < LH; ++i) {
+            const int ii = min(i, L - 1);
+            wq[i] = i < L ? wk_[ii] : zero;
+            mq[i] = i < L ? mk[ii] : one;
+        }
     }
+    auto W_ = [&](int i) -> C {
+        if (HOLD) return wq[i < LH ? i : 0];
+        const int ii = min(i, L - 1);
+        return i < L ? wk_[ii] : zero;
+    };
+    auto M_ = [&](int i) -> C {
+        if (HOLD) return mq[i < LH ? i : 0];
+        const int ii = min(i, L - 1);
+        return i < L ? mk[ii] : one;
+    };
 
     // 2. forward elimination: compose this chunk's maps g -> mu (g + w)
     Aff<C> agg; agg.a = one; agg.b = zero;
 #pragma unroll
     for (int i = 0; i < LA; ++i) {
-        agg.b = cfma(mq[i], agg.b, cmul(mq[i], wq[i]));
-        agg.a = cmul(mq[i], agg.a);
+        agg.b = cfma(M_(i), agg.b, cmul(M_(i), W_(i)));
+        agg.a = cmul(M_(i), agg.a);
     }
     PE3D_MARK(2);
     C g = scan_carry<C, true>(agg, geo, scr);
     PE3D_MARK(3);
 #pragma unroll
     for (int i = 0; i < LA; ++i) {
-        g = cfma(mq[i], g, cmul(mq[i], wq[i]));
+        g = cfma(M_(i), g, cmul(M_(i), W_(i)));
         gq[i] = i < L ? g : zero;
     }
     // 3. back substitution: y -> g + mu y, composed from the chunk's end
     agg.a = one; agg.b = zero;
 #pragma unroll
     for (int i = LA - 1; i >= 0; --i) {
-        agg.b = cfma(mq[i], agg.b, gq[i]);
-        agg.a = cmul(mq[i], agg.a);
+        agg.b = cfma(M_(i), agg.b, gq[i]);
+        agg.a = cmul(M_(i), agg.a);
     }
     PE3D_MARK(4);
     C y = scan_carry<C, false>(agg, geo, scr);
@@ -176,8 +193,8 @@ __device__ bool phaseA(const MarchArgs<C>& P, int j, int base, unsigned char* sm
     const C c1 = P.c1, c2p = P.c2p;
 #pragma unroll
     for (int i = LA - 1; i >= 0; --i) {
-        y = cfma(mq[i], y, gq[i]);
-        const C v = cfma(c2p, y, cmul(c1, wq[i]));
+        y = cfma(M_(i), y, gq[i]);
+        const C v = cfma(c2p, y, cmul(c1, W_(i)));
         if (i < L) wk_[i] = v;                              // v_i over w_i
     }
     __syncthreads();
@@ -247,33 +264,41 @@ __device__ bool phaseB(const MarchArgs<C>& P, const CUtensorMap* tmap, int j, in
     const C* mk = smu + r0;
     // rows i >= Lt of the register chunk act as the identity (mu = 1, v = 0)
     const C one = cone<C>(), zero = czero<C>();
-    C vq[LB], mq[LB];
+    // the step's multipliers are shared by all depths: held in registers for
+    // short chunks, read from shared memory (broadcast) for long ones
+    constexpr bool HOLDB = LB <= 9;
+    constexpr int LHB = HOLDB ? LB : 1;
+    C vq[LB], mqh[LHB];
 #pragma unroll
     for (int i = 0; i < LB; ++i) {
         const int ii = min(i, Lt - 1);
         vq[i] = i < Lt ? tk[ii * TZ] : zero;
-        mq[i] = i < Lt ? mk[ii] : one;
+        if (HOLDB && i < LHB) mqh[i] = i < Lt ? mk[ii] : one;
     }
-
+    auto MB_ = [&](int i) -> C {
+        if (HOLDB) return mqh[i < LHB ? i : 0];
+        const int ii = min(i, Lt - 1);
+        return i < Lt ? mk[ii] : one;
+    };
     Aff<C> agg; agg.a = one; agg.b = zero;
 #pragma unroll
     for (int i = 0; i < LB; ++i) {
-        agg.b = cfma(mq[i], agg.b, cmul(mq[i], vq[i]));
-        agg.a = cmul(mq[i], agg.a);
+        agg.b = cfma(MB_(i), agg.b, cmul(MB_(i), vq[i]));
+        agg.a = cmul(MB_(i), agg.a);
     }
     PE3D_MARK(10);
     C gg = scan_carry<C, true>(agg, geo, scr);
     PE3D_MARK(11);
 #pragma unroll
     for (int i = 0; i < LB; ++i) {
-        gg = cfma(mq[i], gg, cmul(mq[i], vq[i]));
+        gg = cfma(MB_(i), gg, cmul(MB_(i), vq[i]));
         vq[i] = i < Lt ? gg : zero;
     }
     agg.a = one; agg.b = zero;
 #pragma unroll
     for (int i = LB - 1; i >= 0; --i) {
-        agg.b = cfma(mq[i], agg.b, vq[i]);
-        agg.a = cmul(mq[i], agg.a);
+        agg.b = cfma(MB_(i), agg.b, vq[i]);
+        agg.a = cmul(MB_(i), agg.a);
     }
     PE3D_MARK(12);
     C y = scan_carry<C, false>(agg, geo, scr);
@@ -281,7 +306,7 @@ __device__ bool phaseB(const MarchArgs<C>& P, const CUtensorMap* tmap, int j, in
     const C nbinv = from64<C>(sc.nbinv);
 #pragma unroll
     for (int i = LB - 1; i >= 0; --i) {
-        y = cfma(mq[i], y, vq[i]);
+        y = cfma(MB_(i), y, vq[i]);
         vq[i] = cmul(nbinv, y);
     }
 
@@ -578,7 +603,7 @@ __device__ __forceinline__ int find_march(const int* pref, int n, int u) {
 }
 
 template <typename C, int LA, int LB>
-__global__ void __launch_bounds__(NT) k_march_batched(const MarchArgs<C>* __restrict__ D, int n,
+__global__ void __launch_bounds__(NT, 2) k_march_batched(const MarchArgs<C>* __restrict__ D, int n,
                                                       const int* __restrict__ pref, int nsteps, unsigned* bar,
                                                       int* status) {
     extern __shared__ __align__(128) unsigned char smem[];

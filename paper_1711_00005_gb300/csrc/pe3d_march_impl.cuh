@@ -178,10 +178,15 @@ int prepare_kernels(const pe3d_plan_s* p) {
         const KernelTable<C>& t = kernels<C>();
         for (int a = 0; a < 4; ++a) {
             PE3D_CUDA(cudaFuncSetAttribute(t.A[a], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BUDGET));
+            PE3D_CUDA(cudaFuncSetAttribute(t.A[a], cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+            PE3D_CUDA(cudaFuncSetAttribute(t.B[a], cudaFuncAttributePreferredSharedMemoryCarveout, 100));
             PE3D_CUDA(cudaFuncSetAttribute(t.B[a], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BUDGET));
             for (int b = 0; b < 4; ++b)
+            {
                 PE3D_CUDA(cudaFuncSetAttribute(t.persist[a][b], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)SMEM_BUDGET));
+                PE3D_CUDA(cudaFuncSetAttribute(t.persist[a][b], cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+            }
         }
         done = true;
     }
