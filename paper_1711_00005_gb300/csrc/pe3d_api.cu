@@ -197,8 +197,8 @@ int pe3d_set_option(pe3d_plan_t p, int option, int value) {
             return PE3D_OK;
         case PE3D_OPT_TTILE:
             if (p->ldz) return fail(PE3D_ERR_STATE, "layout is fixed once the medium is set");
-            if (value != 0 && value != 8 && value != 16 && value != 32)
-                return fail(PE3D_ERR_ARG, "TTILE must be 0, 8, 16 or 32");
+            if (value != 0 && value != 2 && value != 4 && value != 8 && value != 16 && value != 32)
+                return fail(PE3D_ERR_ARG, "TTILE must be 0, 2, 4, 8, 16 or 32");
             p->ttile = value;
             return PE3D_OK;
         case PE3D_OPT_TIMING:
@@ -377,11 +377,100 @@ int pe3d_plan_info(pe3d_plan_t p, int64_t* info, int n) {
     return cnt;
 }
 
+// Release the layout-dependent buffers so the next pe3d_set_medium (or the
+// autotuner) lays the plan out again.
+static void drop_layout(pe3d_plan_s* p) {
+    const size_t fb = (size_t)p->Nt * p->ldz * elem_bytes(p);
+    dev_free(p, &p->w, fb);
+    dev_free(p, &p->v, fb);
+    dev_free(p, &p->mz, p->mz_bytes);
+    p->mz_bytes = 0;
+    dev_free(p, &p->rc_up, fb);
+    dev_free(p, &p->rc_ut, fb);
+    dev_free(p, &p->rc_db, fb);
+    void** bufs[5] = {&p->mB, &p->zsm, &p->gscr, &p->sc, (void**)&p->slice_of_step};
+    for (int i = 0; i < 5; ++i) {   // per-step tables depend on NtP
+        if (*bufs[i]) { cudaFree(*bufs[i]); *bufs[i] = nullptr; }
+    }
+    p->step_cap = 0;
+    p->ldz = 0;
+    p->medium_ready = false;
+}
+
+// Lay out and set up the plan for (T, TZ) from the device copy of n^2.
+static int relayout(pe3d_plan_s* p, int T, int TZ) {
+    cudaStreamSynchronize(p->stream);
+    drop_layout(p);
+    p->zthreads = T;
+    p->ttile = TZ;
+    int rc = fix_layout(p);
+    if (rc) return rc;
+    const size_t mb = (size_t)p->nslices * p->Nt * p->ldz * elem_bytes(p);
+    if ((rc = dev_alloc(p, &p->mz, mb))) return rc;
+    p->mz_bytes = mb;
+    PE3D_CUDA(cudaMemsetAsync(p->status, 0, sizeof(int), p->stream));
+    rc = p->precision == PE3D_FP32 ? setupA_f32(p) : setupA_f64(p);
+    if (rc) return rc;
+    rc = read_status(p);
+    if (rc) return rc;
+    p->medium_ready = true;
+    return PE3D_OK;
+}
+
 int pe3d_autotune(pe3d_plan_t p, double r0, int steps) {
     g_err.clear();
-    (void)r0; (void)steps;
     if (!p) return fail(PE3D_ERR_ARG, "plan is NULL");
-    return fail(PE3D_ERR_STATE, "autotune not built yet");
+    if (!p->medium_ready || !p->n2) return fail(PE3D_ERR_STATE, "pe3d_set_medium must succeed before pe3d_autotune");
+    if (steps < 1 || !(r0 > 0)) return fail(PE3D_ERR_ARG, "steps must be >= 1 and r0 > 0");
+    const int T0 = p->T, TZ0 = p->TZ, z0 = p->zthreads, t0 = p->ttile, timing0 = p->timing, exec0 = p->exec;
+    cudaEvent_t a = nullptr, b = nullptr;
+    PE3D_CUDA(cudaEventCreate(&a));
+    PE3D_CUDA(cudaEventCreate(&b));
+    const size_t fbytes = (size_t)p->Nt * p->Nz * elem_bytes(p);
+    void* u0 = nullptr;
+    int rc = dev_alloc(p, &u0, fbytes);
+    if (!rc) {   // the timed marches start from a zero field (timing does not depend on values)
+        cudaError_t e = cudaMemsetAsync(u0, 0, fbytes, p->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "memset");
+    }
+    float best = 1e30f;
+    int bestT = T0, bestTZ = TZ0;
+    const int Ts[4] = {32, 64, 128, 256}, TZs[5] = {2, 4, 8, 16, 32};
+    for (int ti = 0; ti < 4 && !rc; ++ti) {
+        for (int zi = 0; zi < 5 && !rc; ++zi) {
+            if (relayout(p, Ts[ti], TZs[zi]) != PE3D_OK) { g_err.clear(); continue; }   // layout does not fit
+            p->timing = 0;
+            float ms = 0.f;
+            int r2 = p->precision == PE3D_FP32 ? march_f32(p, u0, r0, steps, steps + 1, nullptr, p->Nz)
+                                               : march_f64(p, u0, r0, steps, steps + 1, nullptr, p->Nz);
+            if (r2 == PE3D_OK) {   // second run timed (the first warms up)
+                cudaEventRecord(a, p->stream);
+                r2 = p->precision == PE3D_FP32 ? march_f32(p, u0, r0, steps, steps + 1, nullptr, p->Nz)
+                                               : march_f64(p, u0, r0, steps, steps + 1, nullptr, p->Nz);
+                cudaEventRecord(b, p->stream);
+                if (r2 == PE3D_OK) r2 = read_status(p);
+                if (r2 == PE3D_OK && cudaEventElapsedTime(&ms, a, b) == cudaSuccess && ms < best) {
+                    best = ms;
+                    bestT = Ts[ti];
+                    bestTZ = TZs[zi];
+                }
+            }
+            if (r2 != PE3D_OK) { g_err.clear(); cudaGetLastError(); }
+        }
+    }
+    if (u0) dev_free(p, &u0, fbytes);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    p->timing = timing0;
+    p->exec = exec0;
+    if (!rc) rc = relayout(p, bestT, bestTZ);
+    if (rc) {   // restore the caller's choice
+        relayout(p, T0, TZ0);
+        p->zthreads = z0;
+        p->ttile = t0;
+        return rc;
+    }
+    return PE3D_OK;
 }
 
 }  // extern "C"

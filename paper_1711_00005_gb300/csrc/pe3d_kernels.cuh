@@ -20,6 +20,8 @@
 // mu (8 B in complex FP32): 40 B of HBM/L2 traffic per grid-point range-step
 // (w read, mu read, v write, v read, w write).
 #pragma once
+#include <type_traits>
+
 #include "pe3d_device.cuh"
 
 namespace pe3d {
@@ -144,6 +146,10 @@ __device__ bool phaseA(const MarchArgs<C>& P, int j, int base, unsigned char* sm
     // the running solution and stream w and mu from shared memory, which keeps
     // registers low enough for two CTAs per SM on throughput-bound batches.
     constexpr bool HOLD = LA <= 9;
+    // FP64: past-the-end positions skip their (identity) arithmetic with a
+    // uniform branch -- the FP64 pipe is the bottleneck there; FP32 keeps the
+    // branch-free form so loads can be scheduled ahead
+    constexpr bool SKIP = sizeof(C) == 16;
     constexpr int LH = HOLD ? LA : 1;
     C wq[LH], mq[LH], gq[LA];
     if (HOLD) {
@@ -165,37 +171,51 @@ __device__ bool phaseA(const MarchArgs<C>& P, int j, int base, unsigned char* sm
         return i < L ? mk[ii] : one;
     };
 
-    // 2. forward elimination: compose this chunk's maps g -> mu (g + w)
-    Aff<C> agg; agg.a = one; agg.b = zero;
-#pragma unroll
-    for (int i = 0; i < LA; ++i) {
-        agg.b = cfma(M_(i), agg.b, cmul(M_(i), W_(i)));
-        agg.a = cmul(M_(i), agg.a);
-    }
-    PE3D_MARK(2);
-    C g = scan_carry<C, true>(agg, geo, scr);
-    PE3D_MARK(3);
-#pragma unroll
-    for (int i = 0; i < LA; ++i) {
-        g = cfma(M_(i), g, cmul(M_(i), W_(i)));
-        gq[i] = i < L ? g : zero;
-    }
-    // 3. back substitution: y -> g + mu y, composed from the chunk's end
-    agg.a = one; agg.b = zero;
-#pragma unroll
-    for (int i = LA - 1; i >= 0; --i) {
-        agg.b = cfma(M_(i), agg.b, gq[i]);
-        agg.a = cmul(M_(i), agg.a);
-    }
-    PE3D_MARK(4);
-    C y = scan_carry<C, false>(agg, geo, scr);
-    PE3D_MARK(5);
-    const C c1 = P.c1, c2p = P.c2p;
-#pragma unroll
-    for (int i = LA - 1; i >= 0; --i) {
-        y = cfma(M_(i), y, gq[i]);
-        const C v = cfma(c2p, y, cmul(c1, W_(i)));
-        if (i < L) wk_[i] = v;                              // v_i over w_i
+    // the passes, instantiated with and without skipping (see SKIP)
+    auto passes = [&](auto skip_tag) {
+        constexpr bool SK = decltype(skip_tag)::value;
+        // 2. forward elimination: compose this chunk's maps g -> mu (g + w)
+        Aff<C> agg; agg.a = one; agg.b = zero;
+    #pragma unroll
+        for (int i = 0; i < LA; ++i) {
+            if (SK && i >= L) continue;
+            agg.b = cfma(M_(i), agg.b, cmul(M_(i), W_(i)));
+            agg.a = cmul(M_(i), agg.a);
+        }
+        PE3D_MARK(2);
+        C g = scan_carry<C, true>(agg, geo, scr);
+        PE3D_MARK(3);
+    #pragma unroll
+        for (int i = 0; i < LA; ++i) {
+            if (SK && i >= L) { gq[i] = zero; continue; }
+            g = cfma(M_(i), g, cmul(M_(i), W_(i)));
+            gq[i] = i < L ? g : zero;
+        }
+        // 3. back substitution: y -> g + mu y, composed from the chunk's end
+        agg.a = one; agg.b = zero;
+    #pragma unroll
+        for (int i = LA - 1; i >= 0; --i) {
+            if (SK && i >= L) continue;
+            agg.b = cfma(M_(i), agg.b, gq[i]);
+            agg.a = cmul(M_(i), agg.a);
+        }
+        PE3D_MARK(4);
+        C y = scan_carry<C, false>(agg, geo, scr);
+        PE3D_MARK(5);
+        const C c1 = P.c1, c2p = P.c2p;
+    #pragma unroll
+        for (int i = LA - 1; i >= 0; --i) {
+            if (SK && i >= L) continue;
+            y = cfma(M_(i), y, gq[i]);
+            const C v = cfma(c2p, y, cmul(c1, W_(i)));
+            if (i < L) wk_[i] = v;                              // v_i over w_i
+        }
+    };
+    if constexpr (SKIP) {
+        if (L < LA) passes(std::true_type{});
+        else passes(std::false_type{});
+    } else {
+        passes(std::false_type{});
     }
     __syncthreads();
     PE3D_MARK(6);
@@ -267,6 +287,7 @@ __device__ bool phaseB(const MarchArgs<C>& P, const CUtensorMap* tmap, int j, in
     // the step's multipliers are shared by all depths: held in registers for
     // short chunks, read from shared memory (broadcast) for long ones
     constexpr bool HOLDB = LB <= 9;
+    constexpr bool SKIPB = sizeof(C) == 16;      // as in the depth phase
     constexpr int LHB = HOLDB ? LB : 1;
     C vq[LB], mqh[LHB];
 #pragma unroll
@@ -280,36 +301,48 @@ __device__ bool phaseB(const MarchArgs<C>& P, const CUtensorMap* tmap, int j, in
         const int ii = min(i, Lt - 1);
         return i < Lt ? mk[ii] : one;
     };
-    Aff<C> agg; agg.a = one; agg.b = zero;
-#pragma unroll
-    for (int i = 0; i < LB; ++i) {
-        agg.b = cfma(MB_(i), agg.b, cmul(MB_(i), vq[i]));
-        agg.a = cmul(MB_(i), agg.a);
+    auto passes = [&](auto skip_tag) {
+        constexpr bool SK = decltype(skip_tag)::value;
+        Aff<C> agg; agg.a = one; agg.b = zero;
+    #pragma unroll
+        for (int i = 0; i < LB; ++i) {
+            if (SK && i >= Lt) continue;
+            agg.b = cfma(MB_(i), agg.b, cmul(MB_(i), vq[i]));
+            agg.a = cmul(MB_(i), agg.a);
+        }
+        PE3D_MARK(10);
+        C gg = scan_carry<C, true>(agg, geo, scr);
+        PE3D_MARK(11);
+    #pragma unroll
+        for (int i = 0; i < LB; ++i) {
+            if (SK && i >= Lt) continue;
+            gg = cfma(MB_(i), gg, cmul(MB_(i), vq[i]));
+            vq[i] = i < Lt ? gg : zero;
+        }
+        agg.a = one; agg.b = zero;
+    #pragma unroll
+        for (int i = LB - 1; i >= 0; --i) {
+            if (SK && i >= Lt) continue;
+            agg.b = cfma(MB_(i), agg.b, vq[i]);
+            agg.a = cmul(MB_(i), agg.a);
+        }
+        PE3D_MARK(12);
+        C y = scan_carry<C, false>(agg, geo, scr);
+        PE3D_MARK(13);
+        const C nbinv = from64<C>(sc.nbinv);
+    #pragma unroll
+        for (int i = LB - 1; i >= 0; --i) {
+            if (SK && i >= Lt) continue;
+            y = cfma(MB_(i), y, vq[i]);
+            vq[i] = cmul(nbinv, y);
+        }
+    };
+    if constexpr (SKIPB) {
+        if (Lt < LB) passes(std::true_type{});
+        else passes(std::false_type{});
+    } else {
+        passes(std::false_type{});
     }
-    PE3D_MARK(10);
-    C gg = scan_carry<C, true>(agg, geo, scr);
-    PE3D_MARK(11);
-#pragma unroll
-    for (int i = 0; i < LB; ++i) {
-        gg = cfma(MB_(i), gg, cmul(MB_(i), vq[i]));
-        vq[i] = i < Lt ? gg : zero;
-    }
-    agg.a = one; agg.b = zero;
-#pragma unroll
-    for (int i = LB - 1; i >= 0; --i) {
-        agg.b = cfma(MB_(i), agg.b, vq[i]);
-        agg.a = cmul(MB_(i), agg.a);
-    }
-    PE3D_MARK(12);
-    C y = scan_carry<C, false>(agg, geo, scr);
-    PE3D_MARK(13);
-    const C nbinv = from64<C>(sc.nbinv);
-#pragma unroll
-    for (int i = LB - 1; i >= 0; --i) {
-        y = cfma(MB_(i), y, vq[i]);
-        vq[i] = cmul(nbinv, y);
-    }
-
     if (P.periodic) {
         // Sherman-Morrison: u = y - f z, f = (y_0 + (e/gamma) y_{N-1}) xi, in FP64
         const int rl = Nt - 1 - r0;                  // local index of row Nt-1, if ours

@@ -58,9 +58,9 @@ int layout_choose(pe3d_plan_s* p) {
     p->ldz = p->T * p->L;
     p->NG = NT / p->T;
 
-    const int tz_cand[3] = {8, 16, 32};
+    const int tz_cand[5] = {8, 16, 32, 4, 2};
     int tz = -1;
-    for (int ci = 0; ci < 3; ++ci) {
+    for (int ci = 0; ci < 5; ++ci) {
         const int TZ = tz_cand[ci];
         if (p->ttile && TZ != p->ttile) continue;
         const int K = NT / TZ;

@@ -83,7 +83,7 @@ def test_parity_random(P, oracle_lib, case, fp32):
 
 
 @pytest.mark.parametrize("zthreads", [32, 64, 128, 256])
-@pytest.mark.parametrize("ttile", [8, 16, 32])
+@pytest.mark.parametrize("ttile", [2, 4, 8, 16, 32])
 @pytest.mark.parametrize("exec_mode", [1, 2, 3], ids=["stream", "graph", "persistent"])
 def test_layouts_and_exec_modes(P, oracle_lib, zthreads, ttile, exec_mode):
     wl = workloads.random_case(411, 45, periodic=(ttile == 16), K=2, steps=7, seed=40 + zthreads + ttile,
@@ -298,3 +298,20 @@ def test_residual_correction_needs_persistent(P):
     with pytest.raises(P.PE3DError) as e:
         _march_rc(P, wl, 2, exec_mode=P.PE3D_EXEC_STREAM)
     assert e.value.code == P.PE3D_ERR_ARG
+
+
+@pytest.mark.parametrize("fp32", [False, True], ids=["fp64", "fp32"])
+def test_autotune_keeps_parity(P, oracle_lib, fp32):
+    """The autotuner times candidate layouts on the plan's own medium, keeps the
+    fastest, and the march still matches the oracle."""
+    wl = workloads.random_case(301, 67, periodic=fp32, K=3, steps=9, seed=500, stride=3)
+    ref = oracle_lib.march(wl.grid, wl.n2, wl.slice_r, wl.u0)
+    g = wl.grid
+    cdt = np.complex64 if fp32 else np.complex128
+    with P.Plan.for_grid(g, fp32=fp32) as plan:
+        plan.set_medium(torch.from_numpy(wl.n2).cuda(), wl.slice_r)
+        P.pe3d_autotune(plan.h, g.r0, 6)
+        info = plan.info()
+        assert info["zthreads"] in (32, 64, 128, 256) and info["ttile"] in (2, 4, 8, 16, 32)
+        out = plan.march(torch.from_numpy(wl.u0.astype(cdt)).cuda(), g.r0, g.steps, g.stride).cpu().numpy()
+    assert relerrs(out, ref).max() < (TOL32 if fp32 else TOL64)
