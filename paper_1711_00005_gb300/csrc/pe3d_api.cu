@@ -90,7 +90,7 @@ static bool on_device_ptr(const void* ptr) {
 
 // The azimuth tile of v as a 2-D tensor for TMA: x = depth in 8-byte units
 // (a complex64 is one unit, a complex128 two), y = azimuth; box TZ x BY.
-int encode_tmap_v(pe3d_plan_s* p) {
+int encode_tmaps(pe3d_plan_s* p) {
     using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -130,7 +130,7 @@ static int fix_layout(pe3d_plan_s* p) {
     if ((rc = dev_alloc(p, &p->v, fb))) return rc;
     PE3D_CUDA(cudaMemsetAsync(p->w, 0, fb, p->stream));
     PE3D_CUDA(cudaMemsetAsync(p->v, 0, fb, p->stream));
-    return encode_tmap_v(p);
+    return encode_tmaps(p);
 }
 
 static int read_status(pe3d_plan_s* p) {
@@ -434,30 +434,38 @@ int pe3d_autotune(pe3d_plan_t p, double r0, int steps) {
         if (e != cudaSuccess) rc = cuda_fail(e, "memset");
     }
     float best = 1e30f;
-    int bestT = T0, bestTZ = TZ0;
+    int bestT = T0, bestTZ = TZ0, bestC = p->ctas_per_sm;
     const int Ts[4] = {32, 64, 128, 256}, TZs[5] = {2, 4, 8, 16, 32};
+    // the persistent march also tries two CTAs per SM
+    const bool persistent = p->exec == PE3D_EXEC_AUTO || p->exec == PE3D_EXEC_PERSISTENT;
+    const int ncand = persistent ? 2 : 1;
     for (int ti = 0; ti < 4 && !rc; ++ti) {
         for (int zi = 0; zi < 5 && !rc; ++zi) {
             if (relayout(p, Ts[ti], TZs[zi]) != PE3D_OK) { g_err.clear(); continue; }   // layout does not fit
-            p->timing = 0;
-            float ms = 0.f;
-            int r2 = p->precision == PE3D_FP32 ? march_f32(p, u0, r0, steps, steps + 1, nullptr, p->Nz)
-                                               : march_f64(p, u0, r0, steps, steps + 1, nullptr, p->Nz);
-            if (r2 == PE3D_OK) {   // second run timed (the first warms up)
-                cudaEventRecord(a, p->stream);
-                r2 = p->precision == PE3D_FP32 ? march_f32(p, u0, r0, steps, steps + 1, nullptr, p->Nz)
-                                               : march_f64(p, u0, r0, steps, steps + 1, nullptr, p->Nz);
-                cudaEventRecord(b, p->stream);
-                if (r2 == PE3D_OK) r2 = read_status(p);
-                if (r2 == PE3D_OK && cudaEventElapsedTime(&ms, a, b) == cudaSuccess && ms < best) {
-                    best = ms;
-                    bestT = Ts[ti];
-                    bestTZ = TZs[zi];
+            for (int ci = 0; ci < ncand; ++ci) {
+                p->ctas_per_sm = ci + 1;
+                p->timing = 0;
+                float ms = 0.f;
+                int r2 = p->precision == PE3D_FP32 ? march_f32(p, u0, r0, steps, steps + 1, nullptr, p->Nz)
+                                                   : march_f64(p, u0, r0, steps, steps + 1, nullptr, p->Nz);
+                if (r2 == PE3D_OK) {   // second run timed (the first warms up)
+                    cudaEventRecord(a, p->stream);
+                    r2 = p->precision == PE3D_FP32 ? march_f32(p, u0, r0, steps, steps + 1, nullptr, p->Nz)
+                                                   : march_f64(p, u0, r0, steps, steps + 1, nullptr, p->Nz);
+                    cudaEventRecord(b, p->stream);
+                    if (r2 == PE3D_OK) r2 = read_status(p);
+                    if (r2 == PE3D_OK && cudaEventElapsedTime(&ms, a, b) == cudaSuccess && ms < best) {
+                        best = ms;
+                        bestT = Ts[ti];
+                        bestTZ = TZs[zi];
+                        bestC = ci + 1;
+                    }
                 }
+                if (r2 != PE3D_OK) { g_err.clear(); cudaGetLastError(); }
             }
-            if (r2 != PE3D_OK) { g_err.clear(); cudaGetLastError(); }
         }
     }
+    p->ctas_per_sm = bestC;
     if (u0) dev_free(p, &u0, fbytes);
     cudaEventDestroy(a);
     cudaEventDestroy(b);

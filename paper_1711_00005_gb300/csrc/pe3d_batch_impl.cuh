@@ -50,15 +50,31 @@ int launch_batched(pe3d_plan_s* owner, std::vector<MarchArgs<C>>& descs, int nst
     if (n < 1 || n > BATCH_MAX) return fail(PE3D_ERR_ARG, "a batch holds 1 to 64 marches");
     std::vector<int> pref(2 * (n + 1), 0);
     int ca = 0, cb = 0;
-    size_t smem = 0;
+    size_t sA = 0, sB = 0, sC = 0;
+    int NGm = 1, TZm = 2;
     for (int i = 0; i < n; ++i) {
         const MarchArgs<C>& A = descs[i];
         pref[i + 1] = pref[i] + (A.Nt + A.NG - 1) / A.NG;
         pref[n + 1 + i + 1] = pref[n + 1 + i] + A.tiles;
         ca = std::max(ca, batch_class(A.L));
         cb = std::max(cb, batch_class(A.Lt));
-        smem = std::max(smem, std::max(smemA_bytes<C>(A.NG, A.ldz, A.T), smemB_bytes<C>(A.rowsB, A.TZ, A.NtP)));
+        sA = std::max(sA, (size_t)A.NG * grpA_bytes<C>(A.ldz));
+        sB = std::max(sB, tile_bytes<C>(A.rowsB, A.TZ));
+        sC = std::max(sC, coef_bytes<C>(A.NtP, A.periodic));
+        NGm = std::max(NGm, A.NG);
+        TZm = std::max(TZm, A.TZ);
     }
+    // One shared-memory plan for the whole batch (its largest march): two
+    // CTAs per SM when the buffers fit in half an SM, double-buffered if that
+    // fits too; otherwise one CTA per SM with double buffers.
+    SmemPlan sp{};
+    const int units = std::max(pref[n], pref[2 * n + 1]);
+    const bool many = units > 2 * owner->num_sms;
+    if (!plan_smem_sizes<C>(sA, sB, sC, NGm, TZm, many, many, false, false, SMEM_HALF, &sp) &&
+        !plan_smem_sizes<C>(sA, sB, sC, NGm, TZm, true, true, false, false, SMEM_BUDGET, &sp))
+        return fail(PE3D_ERR_ARG, "a batch member is too large for the shared-memory budget");
+    for (auto& d : descs) d.sp = sp;
+    const size_t smem = sp.total;
     const size_t dbytes = sizeof(MarchArgs<C>) * n;
     const size_t need = dbytes + sizeof(int) * pref.size();
     if (need > *devbuf_bytes) {

@@ -191,6 +191,16 @@ __device__ __forceinline__ void tma_g2s_2d(void* dst, const CUtensorMap* map, in
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
 }
+// raise the transaction count of the current phase without arriving
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// make this thread's generic shared-memory writes visible to the async proxy
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // order this thread's generic-proxy view before its later async-proxy accesses
 __device__ __forceinline__ void fence_proxy_async_all() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -199,14 +209,34 @@ __device__ __forceinline__ void fence_proxy_async_all() {
 
 constexpr long long MBAR_SPIN_LIMIT = 1ll << 22;
 
-// Optional sub-step timestamps (build with -DPE3D_TRACE): thread 0 of each
-// CTA records clock64() into slot s of its row of pe3d_trace.
+// Optional sub-step timing (build with -DPE3D_TRACE): thread 0 of each CTA
+// adds the SM cycles since its previous mark to slot s of a per-CTA shared
+// accumulator and copies it to its row of pe3d_trace (a plain store, off the
+// critical path), so a slot holds the time of the interval ending at mark s
+// summed over every unit and range step of the launch.
 #ifdef PE3D_TRACE
 constexpr int TRACE_SLOTS = 24;
 __device__ long long pe3d_trace[4096 * TRACE_SLOTS];
-#define PE3D_MARK(s) \
-    do { if (threadIdx.x == 0 && blockIdx.x < 4096) pe3d::pe3d_trace[blockIdx.x * pe3d::TRACE_SLOTS + (s)] = clock64(); } while (0)
+__shared__ long long pe3d_trace_acc[TRACE_SLOTS + 1];   // [TRACE_SLOTS] holds the last mark
+#define PE3D_TRACE_INIT()                                                                       \
+    do {                                                                                        \
+        if (threadIdx.x == 0) {                                                                 \
+            for (int s_ = 0; s_ < pe3d::TRACE_SLOTS; ++s_) pe3d::pe3d_trace_acc[s_] = 0;         \
+            pe3d::pe3d_trace_acc[pe3d::TRACE_SLOTS] = clock64();                                \
+        }                                                                                       \
+    } while (0)
+#define PE3D_MARK(s)                                                                            \
+    do {                                                                                        \
+        if (threadIdx.x == 0 && blockIdx.x < 4096) {                                            \
+            const long long t_ = clock64();                                                     \
+            const long long a_ = pe3d::pe3d_trace_acc[(s)] + t_ - pe3d::pe3d_trace_acc[pe3d::TRACE_SLOTS]; \
+            pe3d::pe3d_trace_acc[(s)] = a_;                                                     \
+            pe3d::pe3d_trace_acc[pe3d::TRACE_SLOTS] = t_;                                       \
+            pe3d::pe3d_trace[blockIdx.x * pe3d::TRACE_SLOTS + (s)] = a_;                        \
+        }                                                                                       \
+    } while (0)
 #else
+#define PE3D_TRACE_INIT() do { } while (0)
 #define PE3D_MARK(s) do { } while (0)
 #endif
 
@@ -229,6 +259,13 @@ struct StepConst {
     double2 qnext;   // d c_{j+1} / 4: [1 + (d/4) Y] of the next step
     double2 bg;      // e_B / gamma  (cyclic: v^T y = y_0 + bg y_{N-1})
     double2 xi;      // 1 / (1 + v^T z) (cyclic)
+    float2 nbinv32;  // nbinv and qnext rounded once to complex64 (the FP32 march
+    float2 qnext32;  // reads these instead of converting per thread)
 };
+// the step constants in the march type
+__device__ __forceinline__ float2 step_nbinv(const StepConst* s, float2) { return s->nbinv32; }
+__device__ __forceinline__ double2 step_nbinv(const StepConst* s, double2) { return s->nbinv; }
+__device__ __forceinline__ float2 step_qnext(const StepConst* s, float2) { return s->qnext32; }
+__device__ __forceinline__ double2 step_qnext(const StepConst* s, double2) { return s->qnext; }
 
 }  // namespace pe3d

@@ -4,6 +4,7 @@
 namespace pe3d_host {
 int layout_choose_f32(pe3d_plan_s* p) { return layout_choose<float2>(p); }
 int setupA_f32(pe3d_plan_s* p) { return setupA<float2>(p); }
+void persistent_config_f32(const pe3d_plan_s* p, SmemPlan* sp, int* grid) { persistent_config<float2>(p, sp, grid); }
 int march_f32(pe3d_plan_s* p, const void* u0, double r0, int steps, int stride, void* snap, int snap_ld) {
     return march<float2>(p, u0, r0, steps, stride, snap, snap_ld);
 }
@@ -21,10 +22,12 @@ int static_kernels_f32(StaticKernels* k) {
 }  // namespace pe3d_host
 
 #ifdef PE3D_TRACE
-// tracing builds only: copy the FP32 kernels' sub-step timestamps to the host
+// tracing builds only: copy the FP32 kernels' accumulated sub-step cycles to the host and clear them
 extern "C" int pe3d_trace_read(void* host, size_t bytes) {
     PE3D_CUDA(cudaDeviceSynchronize());
     PE3D_CUDA(cudaMemcpyFromSymbol(host, pe3d::pe3d_trace, bytes));
+    static long long zeros[4096 * pe3d::TRACE_SLOTS];
+    PE3D_CUDA(cudaMemcpyToSymbol(pe3d::pe3d_trace, zeros, sizeof(zeros)));
     return PE3D_OK;
 }
 #endif

@@ -23,6 +23,7 @@ struct pe3d_plan_s {
     int exec = PE3D_EXEC_AUTO;
     int zthreads = 0;       // 0 = library choice
     int ttile = 0;          // 0 = library choice
+    int ctas_per_sm = 0;    // persistent march: 1 or 2 (0 = 1); set by the autotuner
     int rc_every = 0;
     int timing = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -96,6 +97,13 @@ int batched_f32(int n, pe3d_plan_s* const* plans, const void* const* u0, const d
 int batched_f64(int n, pe3d_plan_s* const* plans, const void* const* u0, const double* r0, const int* steps,
                 const int* stride, void* const* out);
 
+}  // namespace pe3d_host
+namespace pe3d { struct SmemPlan; }
+namespace pe3d_host {
+// grid and shared-memory plan of the persistent march for a laid-out plan
+void persistent_config_f32(const pe3d_plan_s* p, pe3d::SmemPlan* sp, int* grid);
+void persistent_config_f64(const pe3d_plan_s* p, pe3d::SmemPlan* sp, int* grid);
+
 // the compiled kernels of one precision, for launch by pointer
 struct StaticKernels {
     const void* setupA;
@@ -111,6 +119,6 @@ int dev_alloc(pe3d_plan_s* p, void** ptr, size_t bytes);
 void dev_free(pe3d_plan_s* p, void** ptr, size_t bytes);
 int ensure_steps(pe3d_plan_s* p, int steps);
 int active_slice(const std::vector<double>& slice_r, double r);
-int encode_tmap_v(pe3d_plan_s* p);
+int encode_tmaps(pe3d_plan_s* p);   // tmap_v from v and the layout
 
 }  // namespace pe3d_host

@@ -19,6 +19,18 @@
 // Everything the kernels read per element is the field and one multiplier
 // mu (8 B in complex FP32): 40 B of HBM/L2 traffic per grid-point range-step
 // (w read, mu read, v write, v read, w write).
+//
+// Data movement: every unit of work (a group of depth systems in phase A, a
+// depth tile in phase B) arrives in shared memory by TMA (bulk copies of depth
+// columns, 2-D tensor copies of tiles), issued and tracked by thread 0, and
+// leaves with coalesced stores of all threads (measured faster here than TMA
+// stores of the narrow tiles).  A CTA with several units per phase
+// double-buffers them: the next unit's copies are in flight while the
+// current one is solved.  In the persistent
+// single-march kernel a CTA that owns one depth unit keeps that unit's
+// multipliers in shared memory while the medium slice stays the same, and
+// each step's azimuth coefficients are fetched before the grid barrier that
+// precedes the azimuth phase.
 #pragma once
 #include <type_traits>
 
@@ -33,9 +45,31 @@ constexpr int ST_OK = 0;
 constexpr int ST_SINGULAR = -3;   // PE3D_ERR_SINGULAR
 constexpr int ST_TIMEOUT = -4;    // PE3D_ERR_TIMEOUT
 
+// mbarriers in the first 128 bytes of shared memory: phase-A buffers 0/1,
+// phase-B buffers 0/1.  Each thread keeps their phase parities in bits 0-3 of
+// a word `par`; thread 0, which issues every copy, also marks copies in flight
+// there (bit 8+i: arrived on mbarrier i, bit 12+i: bytes expected on i before
+// its arrival) so that an aborting CTA can drain them.
+constexpr int MB_A = 0, MB_B = 2;
+constexpr uint32_t INFLIGHT = 8, PENDING = 12;
+
+// Byte offsets of the shared-memory regions of one CTA.  Phase-B tiles may
+// overlap the phase-A buffers (the grid barrier separates the phases); the
+// coefficient rows and scratch never overlap anything.
+struct SmemPlan {
+    unsigned a[2];      // phase A: NG groups of (w/v column, mu column)
+    unsigned b[2];      // phase B: tile [rowsB][TZ]
+    unsigned coef[2];   // phase B: mu_B row, then the SM vector (full circle)
+    unsigned scrA, scrB, sf;
+    unsigned total;
+    int nbufA, nbufB;   // 1 or 2 buffers per phase
+    int keepA;          // a[0]'s multipliers stay valid across steps
+};
+
 template <typename C>
 struct MarchArgs {
-    CUtensorMap tmap_v;         // v as 2-D (x: depth in 8-B units, y: azimuth)
+    CUtensorMap tmap_v;         // v as 2-D (x: depth in 8-B units, y: azimuth): tile loads
+    SmemPlan sp;
     int Nz, Nt, ldz, periodic;
     // phase A layout: T threads per depth system, chunk L (odd), NG systems per CTA
     int T, L, NG;
@@ -73,65 +107,110 @@ __host__ __device__ constexpr size_t align128(size_t x) { return (x + 127) & ~si
 constexpr int CHUNK_MAX[4] = {5, 9, 17, 33};
 __host__ __device__ constexpr int chunk_class(int L) { return L <= 5 ? 0 : L <= 9 ? 1 : L <= 17 ? 2 : L <= 33 ? 3 : -1; }
 
-// shared memory: [0,128) mbarrier; phase A: NG groups of (w/v, mu) columns
-// then the scan scratch; phase B: tile, mu, z, scan scratch, SM factors
+// region sizes
 template <typename C>
-__host__ __device__ inline size_t smemA_group(int ldz) { return align128((size_t)2 * ldz * sizeof(C)); }
+__host__ __device__ inline size_t grpA_bytes(int ldz) { return align128((size_t)2 * ldz * sizeof(C)); }
 template <typename C>
-__host__ __device__ inline size_t smemA_bytes(int NG, int ldz, int T) {
-    return 128 + (size_t)NG * smemA_group<C>(ldz) + align128((size_t)NG * 16 * sizeof(Aff<C>));
+__host__ __device__ inline size_t tile_bytes(int rowsB, int TZ) { return align128((size_t)rowsB * TZ * sizeof(C)); }
+template <typename C>
+__host__ __device__ inline size_t coef_bytes(int NtP, int periodic) {
+    return align128((size_t)NtP * sizeof(C)) * (periodic ? 2 : 1);
+}
+
+// Lay the regions out within `budget` bytes, given the bytes of one phase-A
+// buffer (sA), one tile (sB) and one set of coefficient rows (sC), and the
+// largest group count NG and tile width TZ they serve.  Tries the wanted
+// buffer counts with the phase-B tiles clear of the phase-A buffers first,
+// then with them overlapping, then fewer buffers.  coefClear keeps the
+// coefficient rows clear of the phase-A buffers (they are then fetched before
+// the barrier that ends phase A); otherwise they sit with the tiles.  keepA
+// needs one phase-A buffer that no tile overlaps.  Returns false if even
+// single buffers do not fit.
+template <typename C>
+__host__ inline bool plan_smem_sizes(size_t sA, size_t sB, size_t sC, int NG, int TZ, bool wantA2, bool wantB2,
+                                     bool wantKeep, bool coefClear, size_t budget, SmemPlan* out) {
+    SmemPlan p{};
+    size_t o = 128;
+    p.scrA = (unsigned)o; o += align128((size_t)NG * 16 * sizeof(Aff<C>));
+    p.scrB = (unsigned)o; o += align128((size_t)TZ * 16 * sizeof(Aff<C>));
+    p.sf = (unsigned)o;   o += align128((size_t)3 * TZ * sizeof(double2));
+    const size_t fixed = o;
+    for (int nA = wantA2 ? 2 : 1; nA >= 1; --nA)
+        for (int nB = wantB2 ? 2 : 1; nB >= 1; --nB)
+            for (int dis = 1; dis >= 0; --dis) {
+                size_t q = fixed;
+                if (coefClear)
+                    for (int i = 0; i < nB; ++i) { p.coef[i] = (unsigned)q; q += sC; }
+                const size_t a0 = q;
+                for (int i = 0; i < nA; ++i) { p.a[i] = (unsigned)q; q += sA; }
+                size_t bq = dis ? q : a0;
+                if (!coefClear)
+                    for (int i = 0; i < nB; ++i) { p.coef[i] = (unsigned)bq; bq += sC; }
+                for (int i = 0; i < nB; ++i) { p.b[i] = (unsigned)bq; bq += sB; }
+                if (nA == 1) p.a[1] = p.a[0];
+                if (nB == 1) { p.b[1] = p.b[0]; p.coef[1] = p.coef[0]; }
+                const size_t tot = q > bq ? q : bq;
+                if (tot > budget) continue;
+                p.total = (unsigned)tot;
+                p.nbufA = nA;
+                p.nbufB = nB;
+                p.keepA = (wantKeep && dis && nA == 1) ? 1 : 0;
+                *out = p;
+                return true;
+            }
+    return false;
 }
 template <typename C>
-struct SmemB {
-    size_t tile, mu, z, scr, sf, total;
-    __host__ __device__ SmemB(int rowsB, int TZ, int NtP) {
-        size_t o = 128;
-        tile = o; o += align128((size_t)rowsB * TZ * sizeof(C));
-        mu = o;   o += align128((size_t)NtP * sizeof(C));
-        z = o;    o += align128((size_t)NtP * sizeof(C));
-        scr = o;  o += align128((size_t)TZ * 16 * sizeof(Aff<C>));
-        sf = o;   o += align128((size_t)2 * TZ * sizeof(double2));
-        total = o;
-    }
-};
-template <typename C>
-__host__ __device__ inline size_t smemB_bytes(int rowsB, int TZ, int NtP) { return SmemB<C>(rowsB, TZ, NtP).total; }
+__host__ inline bool plan_smem(int NG, int ldz, int rowsB, int TZ, int NtP, int periodic, bool wantA2, bool wantB2,
+                               bool wantKeep, bool coefClear, size_t budget, SmemPlan* out) {
+    return plan_smem_sizes<C>((size_t)NG * grpA_bytes<C>(ldz), tile_bytes<C>(rowsB, TZ), coef_bytes<C>(NtP, periodic),
+                              NG, TZ, wantA2, wantB2, wantKeep, coefClear, budget, out);
+}
 
 // ---------------------------------------------------------------------------
 // phase A: depth systems m = base .. base+NG-1 (one group of T threads each);
 // lane k of a group owns elements k*L .. k*L+L-1 of its column (L <= LA).
-// Returns false (uniformly across the CTA) if a bounded wait gave up.
 // ---------------------------------------------------------------------------
+
+// thread 0: copy the unit's columns of w (and of the slice's multipliers if
+// with_mu) into phase-A buffer `buf`
+template <typename C>
+__device__ __forceinline__ void loadA(const MarchArgs<C>& P, int slice, int base, unsigned char* smem, int buf,
+                                      bool with_mu, uint32_t& par) {
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem) + MB_A + buf;
+    par |= 1u << (INFLIGHT + MB_A + buf);
+    const int ldz = P.ldz;
+    const size_t gstride = grpA_bytes<C>(ldz);
+    const C* mz = P.mz + (long long)slice * P.slice_stride;
+    const int nact = min(P.NG, P.Nt - base);
+    const uint32_t colb = (uint32_t)(ldz * sizeof(C));
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(mbar, (with_mu ? 2u : 1u) * nact * colb);
+    for (int g = 0; g < nact; ++g) {
+        C* dw = reinterpret_cast<C*>(smem + P.sp.a[buf] + g * gstride);
+        bulk_g2s(dw, P.w + (size_t)(base + g) * ldz, colb, mbar);
+        if (with_mu) bulk_g2s(dw + ldz, mz + (size_t)(base + g) * ldz, colb, mbar);
+    }
+}
+
+// Solve the unit in buffer `buf` (v over w in place) and store its columns of
+// v.  Returns false (uniformly across the CTA) if the bounded wait for the
+// buffer gave up; on return the buffer is free for the next copy.
 template <typename C, int LA>
-__device__ bool phaseA(const MarchArgs<C>& P, int j, int base, unsigned char* smem, uint32_t& parity) {
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem);
+__device__ bool computeA(const MarchArgs<C>& P, int base, unsigned char* smem, int buf, uint32_t& par) {
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem) + MB_A + buf;
     const int tid = threadIdx.x;
     const int gs = tid / P.T, k = tid - gs * P.T;
-    const int m = base + gs;
-    const bool active = m < P.Nt;
     const int ldz = P.ldz, L = P.L;
-    const size_t gstride = smemA_group<C>(ldz);
-    C* sw = reinterpret_cast<C*>(smem + 128 + gs * gstride);   // w, overwritten by v
+    const size_t gstride = grpA_bytes<C>(ldz);
+    C* sw = reinterpret_cast<C*>(smem + P.sp.a[buf] + gs * gstride);   // w, overwritten by v
     const C* sm = sw + ldz;
-    Aff<C>* scr = reinterpret_cast<Aff<C>*>(smem + 128 + P.NG * gstride) + gs * 16;
+    Aff<C>* scr = reinterpret_cast<Aff<C>*>(smem + P.sp.scrA) + gs * 16;
 
-    // 1. one thread stages every active group's column of w and of the slice's
-    //    multipliers with bulk copies (one round trip)
     PE3D_MARK(0);
-    if (tid == 0) {
-        fence_proxy_async_all();
-        const C* mz = P.mz + (long long)P.slice_of_step[j] * P.slice_stride;
-        const int nact = min(P.NG, P.Nt - base);
-        const uint32_t colb = (uint32_t)(ldz * sizeof(C));
-        mbar_arrive_expect_tx(mbar, 2u * nact * colb);
-        for (int g = 0; g < nact; ++g) {
-            C* dw = reinterpret_cast<C*>(smem + 128 + g * gstride);
-            bulk_g2s(dw, P.w + (size_t)(base + g) * ldz, colb, mbar);
-            bulk_g2s(dw + ldz, mz + (size_t)(base + g) * ldz, colb, mbar);
-        }
-    }
-    const bool ok = mbar_wait_bounded(mbar, parity, P.status, ST_TIMEOUT);
-    parity ^= 1u;
+    const bool ok = mbar_wait_bounded(mbar, (par >> (MB_A + buf)) & 1u, P.status, ST_TIMEOUT);
+    par ^= 1u << (MB_A + buf);
+    par &= ~(1u << (INFLIGHT + MB_A + buf));
     if (!__syncthreads_and(ok)) return false;
     PE3D_MARK(1);
 
@@ -174,7 +253,7 @@ __device__ bool phaseA(const MarchArgs<C>& P, int j, int base, unsigned char* sm
     // the passes, instantiated with and without skipping (see SKIP)
     auto passes = [&](auto skip_tag) {
         constexpr bool SK = decltype(skip_tag)::value;
-        // 2. forward elimination: compose this chunk's maps g -> mu (g + w)
+        // 1. forward elimination: compose this chunk's maps g -> mu (g + w)
         Aff<C> agg; agg.a = one; agg.b = zero;
     #pragma unroll
         for (int i = 0; i < LA; ++i) {
@@ -191,7 +270,7 @@ __device__ bool phaseA(const MarchArgs<C>& P, int j, int base, unsigned char* sm
             g = cfma(M_(i), g, cmul(M_(i), W_(i)));
             gq[i] = i < L ? g : zero;
         }
-        // 3. back substitution: y -> g + mu y, composed from the chunk's end
+        // 2. back substitution: y -> g + mu y, composed from the chunk's end
         agg.a = one; agg.b = zero;
     #pragma unroll
         for (int i = LA - 1; i >= 0; --i) {
@@ -220,13 +299,18 @@ __device__ bool phaseA(const MarchArgs<C>& P, int j, int base, unsigned char* sm
     __syncthreads();
     PE3D_MARK(6);
 
-    // 4. store v (16-B coalesced)
-    if (active) {
-        float4* gv = reinterpret_cast<float4*>(P.v + (size_t)m * ldz);
-        const float4* s4v = reinterpret_cast<const float4*>(sw);
+    // 3. store the unit's columns of v (16-B coalesced), then free the buffer
+    {
+        const int nact = min(P.NG, P.Nt - base);
         const int n16 = (int)(ldz * sizeof(C) / 16);
-        for (int i = k; i < n16; i += P.T) __stcg(gv + i, s4v[i]);
+        const float4* s4 = reinterpret_cast<const float4*>(smem + P.sp.a[buf]);
+        const int g16 = (int)(gstride / 16);
+        for (int i = tid; i < nact * n16; i += NT) {
+            const int gg = i / n16, e = i - gg * n16;
+            __stcg(reinterpret_cast<float4*>(P.v + (size_t)(base + gg) * ldz) + e, s4[gg * g16 + e]);
+        }
     }
+    __syncthreads();
     PE3D_MARK(7);
     return true;
 }
@@ -235,44 +319,83 @@ __device__ bool phaseA(const MarchArgs<C>& P, int j, int base, unsigned char* sm
 // phase B: azimuth systems for depths p0 .. p0+TZ-1 (tile `tile`); thread
 // (g, k) owns rows k*Lt .. k*Lt+Lt-1 of depth p0+g (Lt <= LB).
 // ---------------------------------------------------------------------------
+
+template <typename C>
+__device__ __forceinline__ uint32_t coefB_bytes(const MarchArgs<C>& P) {
+    return (uint32_t)(P.NtP * sizeof(C)) * (P.periodic ? 2u : 1u);
+}
+// thread 0: the coefficient rows of step j (mu_B, and the SM vector on a full
+// circle) into coefficient region `ci`, counted on B buffer `buf`'s mbarrier
+template <typename C>
+__device__ __forceinline__ void copy_coefB(const MarchArgs<C>& P, int j, unsigned char* smem, int buf, int ci) {
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem) + MB_B + buf;
+    const uint32_t rowb = (uint32_t)(P.NtP * sizeof(C));
+    unsigned char* dst = smem + P.sp.coef[ci];
+    bulk_g2s(dst, P.mB + (size_t)j * P.NtP, rowb, mbar);
+    if (P.periodic) bulk_g2s(dst + align128(rowb), P.zsm + (size_t)j * P.NtP, rowb, mbar);
+}
+// thread 0: fetch step j's coefficient rows ahead of the tile (raises the
+// expected bytes of B buffer `buf`'s current phase without arriving; the
+// tile's loadB arrives)
+template <typename C>
+__device__ __forceinline__ void prefetch_coefB(const MarchArgs<C>& P, int j, unsigned char* smem, int buf, int ci,
+                                               uint32_t& par) {
+    par |= 1u << (PENDING + MB_B + buf);
+    fence_proxy_async_smem();
+    mbar_expect_tx(reinterpret_cast<uint64_t*>(smem) + MB_B + buf, coefB_bytes(P));
+    copy_coefB(P, j, smem, buf, ci);
+}
+// thread 0: the tile of v (TMA boxes of BY rows; rows past Nt arrive as
+// zeros) into B buffer `buf`, with the step's coefficient rows into region
+// buf if with_coef
+template <typename C>
+__device__ __forceinline__ void loadB(const MarchArgs<C>& P, const CUtensorMap* tmap, int j, int tile,
+                                      unsigned char* smem, int buf, bool with_coef, uint32_t& par) {
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem) + MB_B + buf;
+    par = (par | (1u << (INFLIGHT + MB_B + buf))) & ~(1u << (PENDING + MB_B + buf));
+    C* tl = reinterpret_cast<C*>(smem + P.sp.b[buf]);
+    const uint32_t boxb = (uint32_t)(P.BY * P.TZ * sizeof(C));
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(mbar, P.nload * boxb + (with_coef ? coefB_bytes(P) : 0u));
+    const int x = tile * P.TZ * (int)(sizeof(C) / 8);
+    for (int q = 0; q < P.nload; ++q) tma_g2s_2d(tl + (size_t)q * P.BY * P.TZ, tmap, x, q * P.BY, mbar);
+    if (with_coef) copy_coefB(P, j, smem, buf, buf);
+}
+
+// Solve the tile in buffer `buf` with the coefficient rows in region `ci`,
+// apply the next step's azimuth stencil and store w; on return the buffer is
+// free for the next copy.
 template <typename C, int LB>
-__device__ bool phaseB(const MarchArgs<C>& P, const CUtensorMap* tmap, int j, int tile, unsigned char* smem,
-                       uint32_t& parity, bool solve_only = false) {
+__device__ bool computeB(const MarchArgs<C>& P, int j, int tile, unsigned char* smem, int buf, int ci,
+                         uint32_t& par, bool solve_only = false) {
     using R = typename real_of<C>::type;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem) + MB_B + buf;
     const int tid = threadIdx.x;
     const int TZ = P.TZ, Nt = P.Nt, NtP = P.NtP, Lt = P.Lt, ldz = P.ldz;
     const int tzs = __ffs(TZ) - 1;                  // TZ is a power of two
     const int g = tid & (TZ - 1), k = tid >> tzs;
     const int p0 = tile * TZ;
-    const SmemB<C> lay(P.rowsB, TZ, NtP);
-    C* tl = reinterpret_cast<C*>(smem + lay.tile);    // [rowsB][TZ]
-    const C* smu = reinterpret_cast<const C*>(smem + lay.mu);
-    const C* sz = reinterpret_cast<const C*>(smem + lay.z);
-    Aff<C>* scr = reinterpret_cast<Aff<C>*>(smem + lay.scr) + g;
-    double2* sf = reinterpret_cast<double2*>(smem + lay.sf);
+    C* tl = reinterpret_cast<C*>(smem + P.sp.b[buf]);                   // [rowsB][TZ]
+    const C* smu = reinterpret_cast<const C*>(smem + P.sp.coef[ci]);
+    const C* sz = reinterpret_cast<const C*>(smem + P.sp.coef[ci] + align128((size_t)NtP * sizeof(C)));
+    Aff<C>* scr = reinterpret_cast<Aff<C>*>(smem + P.sp.scrB) + g;
+    double2* sf = reinterpret_cast<double2*>(smem + P.sp.sf);
+    C* sfc = reinterpret_cast<C*>(sf + 2 * TZ);
+    const StepConst* scp = P.sc + j;
+    // the step constants this thread needs, fetched while the tile is in flight
+    const C nbinv = step_nbinv(scp, C{});
+    const C qn = step_qnext(scp, C{});
+    double2 bg = make_double2(0.0, 0.0), xi = make_double2(0.0, 0.0);
+    if (P.periodic && k == 0) { bg = scp->bg; xi = scp->xi; }
 
-    // 1. the tile of v (TMA boxes of BY rows; rows past Nt arrive as zeros),
-    //    the step's multipliers and, for a full circle, its SM vector
     PE3D_MARK(8);
-    if (tid == 0) {
-        fence_proxy_async_all();
-        const uint32_t boxb = (uint32_t)(P.BY * TZ * sizeof(C));
-        const uint32_t rowb = (uint32_t)(NtP * sizeof(C));
-        mbar_arrive_expect_tx(mbar, P.nload * boxb + rowb * (P.periodic ? 2u : 1u));
-        const int x = p0 * (int)(sizeof(C) / 8);
-        for (int q = 0; q < P.nload; ++q)
-            tma_g2s_2d(tl + (size_t)q * P.BY * TZ, tmap, x, q * P.BY, mbar);
-        bulk_g2s(const_cast<C*>(smu), P.mB + (size_t)j * NtP, rowb, mbar);
-        if (P.periodic) bulk_g2s(const_cast<C*>(sz), P.zsm + (size_t)j * NtP, rowb, mbar);
-    }
     {   // rows the boxes do not cover are zero
         const int r0z = P.nload * P.BY;
         for (int i = r0z * TZ + tid; i < NtP * TZ; i += NT) tl[i] = czero<C>();
     }
-    const StepConst sc = P.sc[j];
-    const bool ok = mbar_wait_bounded(mbar, parity, P.status, ST_TIMEOUT);
-    parity ^= 1u;
+    const bool ok = mbar_wait_bounded(mbar, (par >> (MB_B + buf)) & 1u, P.status, ST_TIMEOUT);
+    par ^= 1u << (MB_B + buf);
+    par &= ~(1u << (INFLIGHT + MB_B + buf));
     if (!__syncthreads_and(ok)) return false;
     PE3D_MARK(9);
 
@@ -329,7 +452,6 @@ __device__ bool phaseB(const MarchArgs<C>& P, const CUtensorMap* tmap, int j, in
         PE3D_MARK(12);
         C y = scan_carry<C, false>(agg, geo, scr);
         PE3D_MARK(13);
-        const C nbinv = from64<C>(sc.nbinv);
     #pragma unroll
         for (int i = LB - 1; i >= 0; --i) {
             if (SK && i >= Lt) continue;
@@ -344,14 +466,26 @@ __device__ bool phaseB(const MarchArgs<C>& P, const CUtensorMap* tmap, int j, in
         passes(std::false_type{});
     }
     if (P.periodic) {
-        // Sherman-Morrison: u = y - f z, f = (y_0 + (e/gamma) y_{N-1}) xi, in FP64
+        // Sherman-Morrison: u = y - f z, f = (y_0 + (e/gamma) y_{N-1}) xi; one
+        // thread per depth forms f in FP64.  Row Nt-1 is picked in the march
+        // type first, so only the two values used are converted (each FP64
+        // instruction costs a warp dozens of cycles on this part)
         const int rl = Nt - 1 - r0;                  // local index of row Nt-1, if ours
-        if (k == 0) sf[g] = to64(vq[0]);
+        C ylast = zero;
 #pragma unroll
         for (int i = 0; i < LB; ++i)
-            if (i < Lt && i == rl) sf[TZ + g] = to64(vq[i]);
+            if (i < Lt && i == rl) ylast = vq[i];
+        if (k == 0) sf[g] = to64(vq[0]);
+        if (rl >= 0 && rl < Lt) sf[TZ + g] = to64(ylast);
         __syncthreads();
-        const C f = from64<C>(cmul(cadd(sf[g], cmul(sc.bg, sf[TZ + g])), sc.xi));
+        if (k == 0) {
+            const double2 y0 = sf[g], yn = sf[TZ + g];
+            const double2 t = make_double2(fma(bg.x, yn.x, fma(-bg.y, yn.y, y0.x)),
+                                           fma(bg.x, yn.y, fma(bg.y, yn.x, y0.y)));
+            sfc[g] = from64<C>(cmul(t, xi));
+        }
+        __syncthreads();
+        const C f = sfc[g];
 #pragma unroll
         for (int i = 0; i < LB; ++i) {
             const int ii = min(i, Lt - 1);
@@ -371,9 +505,9 @@ __device__ bool phaseB(const MarchArgs<C>& P, const CUtensorMap* tmap, int j, in
     // azimuth solve) stores the solution itself into P.w.
     const bool refine_now = !solve_only && P.rc_every > 0 && (j + 1) % P.rc_every == 0;
     const bool refine_next = !solve_only && P.rc_every > 0 && (j + 2) % P.rc_every == 0;
-    const C q = solve_only ? zero : from64<C>(sc.qnext);
+    const C q = solve_only ? zero : qn;
     const bool snap = !solve_only && !refine_now && P.snap != nullptr && ((j + 1) % P.stride) == 0;
-    C* sp = snap ? P.snap + (size_t)((j + 1) / P.stride - 1) * Nt * P.snap_ld + p0 + g : nullptr;
+    C* snp = snap ? P.snap + (size_t)((j + 1) / P.stride - 1) * Nt * P.snap_ld + p0 + g : nullptr;
     const bool col_ok = p0 + g < P.Nz;
     // neighbours across the chunk edges: row r0-1 and row r0+Lt; the row after
     // Nt-1 is row 0 on a full circle and the zero ghost between walls
@@ -395,38 +529,62 @@ __device__ bool phaseB(const MarchArgs<C>& P, const CUtensorMap* tmap, int j, in
         const C wn = refine_now ? vq[i] : cfma(q, lap, vq[i]);
         if (i < Lt && row < Nt) {
             __stcg(wcol + (size_t)i * ldz, wn);
-            if (snap && col_ok) sp[(size_t)row * P.snap_ld] = vq[i];
+            if (snap && col_ok) snp[(size_t)row * P.snap_ld] = vq[i];
             if (ucol) __stcg(ucol + (size_t)i * ldz, vq[i]);
         }
     }
+    __syncthreads();                              // the tile is free for the next copy
     PE3D_MARK(15);
     return true;
 }
 
+// Leave the kernel after a failed bounded wait.  Thread 0 first lets its
+// copies in flight land (bounded waits; a buffer whose bytes were expected
+// before its arrival is arrived on first).
+__device__ __forceinline__ void drain_copies(unsigned char* smem, uint32_t par) {
+    if (threadIdx.x != 0) return;
+    uint64_t* mb = reinterpret_cast<uint64_t*>(smem);
+    for (int i = 0; i < 4; ++i) {
+        if (par & (1u << (PENDING + i)))
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mb + i)) : "memory");
+        if (par & ((1u << (INFLIGHT + i)) | (1u << (PENDING + i))))
+            for (long long s = 0; s < MBAR_SPIN_LIMIT; ++s)
+                if (mbar_try_wait(mb + i, (par >> i) & 1u)) break;
+    }
+}
+#define PE3D_ABORT()                   \
+    do {                               \
+        drain_copies(smem, par);       \
+        return;                        \
+    } while (0)
+
 // ---------------------------------------------------------------------------
-// kernels
+// kernels of the per-phase launch modes (one unit per CTA)
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void init_mbarriers(unsigned char* smem) {
+    if (threadIdx.x == 0)
+        for (int i = 0; i < 4; ++i) mbar_init(reinterpret_cast<uint64_t*>(smem) + i, 1);
+    __syncthreads();
+}
+
 template <typename C, int LA>
 __global__ void __launch_bounds__(NT) k_phaseA(const __grid_constant__ MarchArgs<C> P, int j) {
     extern __shared__ __align__(128) unsigned char smem[];
-    if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t*>(smem), 1);
-    __syncthreads();
-    uint32_t parity = 0;
-    phaseA<C, LA>(P, j, blockIdx.x * P.NG, smem, parity);
+    init_mbarriers(smem);
+    uint32_t par = 0;
+    const int base = blockIdx.x * P.NG;
+    if (threadIdx.x == 0) loadA(P, P.slice_of_step[j], base, smem, 0, true, par);
+    if (!computeA<C, LA>(P, base, smem, 0, par)) drain_copies(smem, par);
 }
 
 template <typename C, int LB>
 __global__ void __launch_bounds__(NT) k_phaseB(const __grid_constant__ MarchArgs<C> P, int j) {
     extern __shared__ __align__(128) unsigned char smem[];
-    if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t*>(smem), 1);
-    __syncthreads();
-    uint32_t parity = 0;
-    phaseB<C, LB>(P, &P.tmap_v, j, blockIdx.x, smem, parity);
+    init_mbarriers(smem);
+    uint32_t par = 0;
+    if (threadIdx.x == 0) loadB(P, &P.tmap_v, j, blockIdx.x, smem, 0, true, par);
+    if (!computeB<C, LB>(P, j, blockIdx.x, smem, 0, 0, par)) drain_copies(smem, par);
 }
-
-// leave the kernel after a failed bounded wait (no copy of this CTA is in
-// flight then: every wait that can fail follows its own copies' completion)
-#define PE3D_ABORT() return
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     unsigned v;
@@ -438,30 +596,39 @@ __device__ __forceinline__ int ld_relaxed(const int* p) {
     asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
-// Grid-wide barrier for a cooperative launch (all CTAs co-resident).  The
-// wait is bounded: after SPIN_LIMIT polls, or once another CTA has flagged
-// an error, it records PE3D_ERR_TIMEOUT and returns false.
-__device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target, int* status) {
-    __shared__ int s_ok;
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident), split in
+// two so thread 0 can issue independent copies in between.  Arrive: every
+// thread orders its generic global writes before later async-proxy (TMA)
+// reads, then one release add.  Wait: acquire polls, bounded: after
+// SPIN_LIMIT polls, or once another CTA has flagged an error, it records
+// PE3D_ERR_TIMEOUT and returns false.
+__device__ __forceinline__ void grid_arrive(unsigned* ctr) {
     asm volatile("fence.proxy.async.global;" ::: "memory");
     __syncthreads();
+    if (threadIdx.x == 0) red_release_add(ctr, 1u);
+}
+__device__ __forceinline__ bool grid_wait(unsigned* ctr, unsigned target, int* status) {
+    __shared__ int s_ok;
     if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(ctr, 1u);
         int ok = 1;
         long long spins = 0;
         while (ld_acquire(ctr) < target) {
             if (++spins > SPIN_LIMIT) { atomicExch(status, ST_TIMEOUT); ok = 0; break; }
             if ((spins & 255) == 0 && ld_relaxed(status) != ST_OK) { ok = 0; break; }
-            if (spins > 32) __nanosleep(32);
         }
-        __threadfence();
         asm volatile("fence.proxy.async.global;" ::: "memory");
         s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
+}
+__device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target, int* status) {
+    grid_arrive(ctr);
+    return grid_wait(ctr, target, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -561,58 +728,110 @@ __device__ void combine_phase(const MarchArgs<C>& P, int j) {
     }
 }
 
-// The whole march in one cooperative launch: two grid barriers per step (six
-// on a corrected step).
+// ---------------------------------------------------------------------------
+// the persistent single march: all range steps in one cooperative launch, two
+// grid barriers per step (six on a corrected step)
+// ---------------------------------------------------------------------------
+
+// Run `compute(u, buf)` on units first, next(first), ... (next returns -1 at
+// the end), with thread 0 issuing `load(u, buf)` one unit ahead when there
+// are two buffers, or right after the previous unit with one (compute
+// returns with its buffer free).  The caller has issued load(first, 0).
+template <typename Load, typename Compute, typename Next>
+__device__ __forceinline__ bool unit_pipeline(int first, int nbuf, Load load, Compute compute, Next next) {
+    int u = first, n = 0;
+    while (u >= 0) {
+        const int un = next(u);
+        const int buf = nbuf > 1 ? (n & 1) : 0;
+        if (nbuf > 1 && un >= 0 && threadIdx.x == 0) load(un, buf ^ 1);
+        if (!compute(u, buf)) return false;
+        if (nbuf == 1 && un >= 0 && threadIdx.x == 0) load(un, 0);
+        u = un;
+        ++n;
+    }
+    return true;
+}
+
 template <typename C, int LA, int LB>
 __global__ void __launch_bounds__(NT) k_march_persistent(const __grid_constant__ MarchArgs<C> P) {
     extern __shared__ __align__(128) unsigned char smem[];
-    if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t*>(smem), 1);
-    __syncthreads();
-    uint32_t parity = 0;
-    const unsigned G = gridDim.x;
+    init_mbarriers(smem);
+    PE3D_TRACE_INIT();
+    uint32_t par = 0;
+    const int G = gridDim.x, bid = blockIdx.x;
     unsigned nb = 0;
     const int unitsA = (P.Nt + P.NG - 1) / P.NG;
+    const bool hasA = bid < unitsA, hasB = bid < P.tiles;
+    const bool keepA = P.sp.keepA && unitsA <= G;     // one depth unit per CTA
+    // thread 0 reads the next step's slice one step ahead
+    int sl_next = (threadIdx.x == 0 && P.j0 < P.j1) ? P.slice_of_step[P.j0] : 0;
+    int sl_held = -1;                                 // slice of the multipliers in a[0] (keepA)
+    if (threadIdx.x == 0 && hasB && P.j0 < P.j1) prefetch_coefB(P, P.j0, smem, 0, 0, par);
+    auto nextA = [&](int u) { return u + G < unitsA ? u + G : -1; };
+    auto nextB = [&](int t) { return t + G < P.tiles ? t + G : -1; };
     for (int j = P.j0; j < P.j1; ++j) {
-        for (int u = blockIdx.x; u < unitsA; u += G) {
-            if (!phaseA<C, LA>(P, j, u * P.NG, smem, parity)) PE3D_ABORT();
-            __syncthreads();
+        const int sl = sl_next;
+        // phase A (Eq. 5)
+        if (hasA && threadIdx.x == 0) {
+            loadA(P, sl, bid * P.NG, smem, 0, !(keepA && sl == sl_held), par);
+            sl_held = keepA ? sl : -1;
+        }
+        // read after the copies are issued: their proxy fence would wait for it
+        if (threadIdx.x == 0 && j + 1 < P.j1) sl_next = P.slice_of_step[j + 1];
+        if (hasA) {
+            const bool ok = unit_pipeline(
+                bid, P.sp.nbufA,
+                [&](int u, int b) { loadA(P, sl, u * P.NG, smem, b, true, par); },
+                [&](int u, int b) { return computeA<C, LA>(P, u * P.NG, smem, b, par); }, nextA);
+            if (!ok) PE3D_ABORT();
         }
         PE3D_MARK(16);
         if (!grid_barrier(P.bar, (++nb) * G, P.status)) PE3D_ABORT();
         PE3D_MARK(17);
-        for (int t = blockIdx.x; t < P.tiles; t += G) {
-            if (!phaseB<C, LB>(P, &P.tmap_v, j, t, smem, parity)) PE3D_ABORT();
-            __syncthreads();
+        // phase B (Eq. 6)
+        if (hasB) {
+            if (threadIdx.x == 0) loadB(P, &P.tmap_v, j, bid, smem, 0, false, par);
+            const bool ok = unit_pipeline(
+                bid, P.sp.nbufB,
+                [&](int t, int b) { loadB(P, &P.tmap_v, j, t, smem, b, false, par); },
+                [&](int t, int b) { return computeB<C, LB>(P, j, t, smem, b, 0, par); }, nextB);
+            if (!ok) PE3D_ABORT();
         }
         PE3D_MARK(18);
-        if (!grid_barrier(P.bar, (++nb) * G, P.status)) PE3D_ABORT();
+        const bool refine = P.rc_every > 0 && (j + 1) % P.rc_every == 0;
+        grid_arrive(P.bar);
+        // the next step's azimuth coefficients, while the barrier completes
+        if (threadIdx.x == 0 && hasB && !refine && j + 1 < P.j1) prefetch_coefB(P, j + 1, smem, 0, 0, par);
+        if (!grid_wait(P.bar, (++nb) * G, P.status)) PE3D_ABORT();
         PE3D_MARK(19);
-        if (P.rc_every > 0 && (j + 1) % P.rc_every == 0) {
+        if (refine) {
             residual_phase(P, j);                                   // r into v
             if (!grid_barrier(P.bar, (++nb) * G, P.status)) PE3D_ABORT();
             MarchArgs<C> Q = P;                                    // A^-1 r into v
             Q.w = P.v;
             Q.c1 = czero<C>();
-            Q.c2p = from64<C>(make_double2(0.0, 0.0));
             {
                 const double s = 1.0 / ((P.k0 * P.dz) * (P.k0 * P.dz));
                 const double2 e = make_double2(0.25 * s, -P.k0 * P.dr / 4.0 * s);
                 const double en = e.x * e.x + e.y * e.y;
                 Q.c2p = from64<C>(make_double2(-e.x / en, e.y / en));   // -1/e
             }
-            for (int u = blockIdx.x; u < unitsA; u += G) {
-                if (!phaseA<C, LA>(Q, j, u * P.NG, smem, parity)) PE3D_ABORT();
-                __syncthreads();
+            for (int u = bid; u < unitsA; u += G) {
+                if (threadIdx.x == 0) loadA(Q, sl, u * P.NG, smem, 0, true, par);
+                if (!computeA<C, LA>(Q, u * P.NG, smem, 0, par)) PE3D_ABORT();
             }
+            sl_held = -1;
             if (!grid_barrier(P.bar, (++nb) * G, P.status)) PE3D_ABORT();
             Q.w = P.db;                                            // B^-1 A^-1 r into db
-            for (int t = blockIdx.x; t < P.tiles; t += G) {
-                if (!phaseB<C, LB>(Q, &P.tmap_v, j, t, smem, parity, true)) PE3D_ABORT();
-                __syncthreads();
+            for (int t = bid; t < P.tiles; t += G) {
+                if (threadIdx.x == 0) loadB(Q, &P.tmap_v, j, t, smem, 0, true, par);
+                if (!computeB<C, LB>(Q, j, t, smem, 0, 0, par, true)) PE3D_ABORT();
             }
             if (!grid_barrier(P.bar, (++nb) * G, P.status)) PE3D_ABORT();
             combine_phase(P, j);
-            if (!grid_barrier(P.bar, (++nb) * G, P.status)) PE3D_ABORT();
+            grid_arrive(P.bar);
+            if (threadIdx.x == 0 && hasB && j + 1 < P.j1) prefetch_coefB(P, j + 1, smem, 0, 0, par);
+            if (!grid_wait(P.bar, (++nb) * G, P.status)) PE3D_ABORT();
         }
     }
 }
@@ -622,7 +841,8 @@ __global__ void __launch_bounds__(NT) k_march_persistent(const __grid_constant__
 // the same launches.  Each step's units (phase A: groups of depth systems,
 // phase B: azimuth tiles) of all marches form one list; D[i].j0/j1 give march
 // i its own step window, so marches that started at different times (the
-// request loop) share a launch.  Two grid barriers per step, as above.
+// request loop) share a launch.  Two grid barriers per step, as above; units
+// are double-buffered across marches when the batch's plan has two buffers.
 // ---------------------------------------------------------------------------
 constexpr int BATCH_MAX = 64;
 
@@ -643,27 +863,56 @@ __global__ void __launch_bounds__(NT, 2) k_march_batched(const MarchArgs<C>* __r
     __shared__ int s_pa[BATCH_MAX + 1], s_pb[BATCH_MAX + 1], s_j0[BATCH_MAX], s_j1[BATCH_MAX];
     for (int i = threadIdx.x; i <= n; i += NT) { s_pa[i] = pref[i]; s_pb[i] = pref[n + 1 + i]; }
     for (int i = threadIdx.x; i < n; i += NT) { s_j0[i] = D[i].j0; s_j1[i] = D[i].j1; }
-    if (threadIdx.x == 0) mbar_init(reinterpret_cast<uint64_t*>(smem), 1);
-    __syncthreads();
-    uint32_t parity = 0;
-    const unsigned G = gridDim.x;
+    init_mbarriers(smem);
+    uint32_t par = 0;
+    const int G = gridDim.x;
+    const int nbufA = D[0].sp.nbufA, nbufB = D[0].sp.nbufB;   // one shared-memory plan for the batch
     unsigned nb = 0;
     for (int t = 0; t < nsteps; ++t) {
-        for (int u = blockIdx.x; u < s_pa[n]; u += G) {
+        // the next unit, from u on in steps of G, of a march inside its window
+        auto activeA = [&](int u) {
+            for (; u < s_pa[n]; u += G) {
+                const int i = find_march(s_pa, n, u);
+                if (s_j0[i] + t < s_j1[i]) return u;
+            }
+            return -1;
+        };
+        auto activeB = [&](int u) {
+            for (; u < s_pb[n]; u += G) {
+                const int i = find_march(s_pb, n, u);
+                if (s_j0[i] + t < s_j1[i]) return u;
+            }
+            return -1;
+        };
+        auto loadUA = [&](int u, int b) {
             const int i = find_march(s_pa, n, u);
-            const int j = s_j0[i] + t;
-            if (j >= s_j1[i]) continue;
-            if (!phaseA<C, LA>(D[i], j, (u - s_pa[i]) * D[i].NG, smem, parity)) PE3D_ABORT();
-            __syncthreads();
-        }
-        if (!grid_barrier(bar, (++nb) * G, status)) PE3D_ABORT();
-        for (int u = blockIdx.x; u < s_pb[n]; u += G) {
+            loadA(D[i], D[i].slice_of_step[s_j0[i] + t], (u - s_pa[i]) * D[i].NG, smem, b, true, par);
+        };
+        auto loadUB = [&](int u, int b) {
             const int i = find_march(s_pb, n, u);
-            const int j = s_j0[i] + t;
-            if (j >= s_j1[i]) continue;
-            if (!phaseB<C, LB>(D[i], &D[i].tmap_v, j, u - s_pb[i], smem, parity)) PE3D_ABORT();
-            __syncthreads();
-        }
+            loadB(D[i], &D[i].tmap_v, s_j0[i] + t, u - s_pb[i], smem, b, true, par);
+        };
+        const int fa = activeA(blockIdx.x);
+        if (fa >= 0 && threadIdx.x == 0) loadUA(fa, 0);
+        bool ok = unit_pipeline(
+            fa, nbufA, loadUA,
+            [&](int u, int b) {
+                const int i = find_march(s_pa, n, u);
+                return computeA<C, LA>(D[i], (u - s_pa[i]) * D[i].NG, smem, b, par);
+            },
+            [&](int u) { return activeA(u + G); });
+        if (!ok) PE3D_ABORT();
+        if (!grid_barrier(bar, (++nb) * G, status)) PE3D_ABORT();
+        const int fb = activeB(blockIdx.x);
+        if (fb >= 0 && threadIdx.x == 0) loadUB(fb, 0);
+        ok = unit_pipeline(
+            fb, nbufB, loadUB,
+            [&](int u, int b) {
+                const int i = find_march(s_pb, n, u);
+                return computeB<C, LB>(D[i], s_j0[i] + t, u - s_pb[i], smem, b, b, par);
+            },
+            [&](int u) { return activeB(u + G); });
+        if (!ok) PE3D_ABORT();
         if (!grid_barrier(bar, (++nb) * G, status)) PE3D_ABORT();
     }
 }
@@ -750,6 +999,8 @@ __global__ void k_setupB(int steps, int Nt, int NtP, int periodic, double k0, do
     out.qnext = make_double2(0.0, kd * cn / 4.0);
     out.bg = make_double2(0.0, 0.0);
     out.xi = make_double2(0.0, 0.0);
+    out.nbinv32 = from64<float2>(out.nbinv);
+    out.qnext32 = from64<float2>(out.qnext);
     C* mrow = mB + (size_t)j * NtP;
     double2 mprev = make_double2(0.0, 0.0);
     bool bad = false;

@@ -10,7 +10,8 @@
 namespace pe3d_host {
 using namespace pe3d;
 
-constexpr size_t SMEM_BUDGET = 200 * 1024;   // dynamic shared memory per CTA we allow
+constexpr size_t SMEM_BUDGET = 225 * 1024;   // dynamic shared memory per CTA (227 KB maximum less static use)
+constexpr size_t SMEM_HALF = 112 * 1024;     // per CTA when two share an SM
 
 inline double2 d2(double x, double y) { return make_double2(x, y); }
 inline double2 h_mul(double2 a, double2 b) { return d2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
@@ -47,7 +48,10 @@ int layout_choose(pe3d_plan_s* p) {
         const int T = cand[ci];
         if (p->zthreads && T != p->zthreads) continue;
         const int L = odd_ceil(p->Nz, T);
-        if (L > 33 || smemA_bytes<C>(NT / T, T * L, T) > SMEM_BUDGET) continue;
+        SmemPlan sp;
+        if (L > 33 || !plan_smem_sizes<C>((size_t)(NT / T) * grpA_bytes<C>(T * L), 0, 0, NT / T, 2, false, false,
+                                          false, false, SMEM_BUDGET, &sp))
+            continue;
         best = T;
         if (p->zthreads || L <= 9) break;
     }
@@ -68,7 +72,10 @@ int layout_choose(pe3d_plan_s* p) {
         const int nload = (p->Nt + 255) / 256;
         const int BY = box_rows(p->Nt, nload, (int)(TZ * sizeof(C)));
         const int rowsB = std::max(K * Lt, nload * BY);
-        if (Lt > 33 || smemB_bytes<C>(rowsB, TZ, K * Lt) > SMEM_BUDGET) continue;
+        SmemPlan sp;
+        if (Lt > 33 || !plan_smem<C>(p->NG, p->ldz, rowsB, TZ, K * Lt, p->boundary == PE3D_PERIODIC, false, false,
+                                     false, false, SMEM_BUDGET, &sp))
+            continue;
         tz = TZ;
         break;
     }
@@ -166,9 +173,44 @@ const KernelTable<C>& kernels() {
     return t;
 }
 
+// Shared-memory plan of the per-phase kernels (one unit per CTA, one buffer each)
 template <typename C>
-size_t smem_persistent(const pe3d_plan_s* p) {
-    return std::max(smemA_bytes<C>(p->NG, p->ldz, p->T), smemB_bytes<C>(p->rowsB, p->TZ, p->NtP));
+SmemPlan single_unit_plan(const pe3d_plan_s* p) {
+    SmemPlan sp{};
+    plan_smem<C>(p->NG, p->ldz, p->rowsB, p->TZ, p->NtP, p->boundary == PE3D_PERIODIC, false, false, false, true,
+                 SMEM_BUDGET, &sp);   // layout_choose guarantees it fits
+    return sp;
+}
+
+// Grid and shared-memory plan of the persistent march with `per` CTAs per
+// SM (or one per unit when there are fewer): units beyond the grid are
+// double-buffered when the buffers fit, and a CTA with a single depth unit
+// keeps its multipliers in shared memory.
+template <typename C>
+void persistent_config_n(const pe3d_plan_s* p, int per, SmemPlan* sp, int* grid) {
+    const int unitsA = (p->Nt + p->NG - 1) / p->NG;
+    const size_t budget = per == 2 ? SMEM_HALF : SMEM_BUDGET;
+    const int G = std::min(per * p->num_sms, std::max(unitsA, p->tiles));
+    if (!plan_smem<C>(p->NG, p->ldz, p->rowsB, p->TZ, p->NtP, p->boundary == PE3D_PERIODIC, unitsA > G,
+                      p->tiles > G, unitsA <= G, true, budget, sp))
+        *sp = single_unit_plan<C>(p);
+    *grid = G;
+}
+template <typename C>
+void persistent_config(const pe3d_plan_s* p, SmemPlan* sp, int* grid) { persistent_config_n<C>(p, 1, sp, grid); }
+
+// The plan's CTAs per SM (ctas_per_sm, 1 by default) if the kernel fits that
+// many on an SM, else one.
+template <typename C>
+int persistent_grid(const pe3d_plan_s* p, SmemPlan* sp, int* grid) {
+    const void* fn = kernels<C>().persist[chunk_class(p->L)][chunk_class(p->Lt)];
+    for (int per = p->ctas_per_sm == 2 ? 2 : 1; per >= 1; --per) {
+        persistent_config_n<C>(p, per, sp, grid);
+        int nb = 0;
+        PE3D_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, NT, sp->total));
+        if (nb >= per) return PE3D_OK;
+    }
+    return fail(PE3D_ERR_ARG, "persistent kernel does not fit on an SM");
 }
 
 template <typename C>
@@ -224,37 +266,24 @@ int launch_prologue(pe3d_plan_s* p, const void* u0_dev, double r0) {
 }
 
 template <typename C>
-int persistent_grid(const pe3d_plan_s* p, int* grid) {
-    int nb = 0;
-    const void* fn = kernels<C>().persist[chunk_class(p->L)][chunk_class(p->Lt)];
-    PE3D_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, NT, smem_persistent<C>(p)));
-    if (nb < 1) return fail(PE3D_ERR_ARG, "persistent kernel does not fit on an SM");
-    const int unitsA = (p->Nt + p->NG - 1) / p->NG;
-    *grid = std::min(nb * p->num_sms, std::max(unitsA, p->tiles));
-    return PE3D_OK;
-}
-
-template <typename C>
 int run_steps(pe3d_plan_s* p, MarchArgs<C>& A, int steps) {
     int exec = p->exec;
     if (exec == PE3D_EXEC_AUTO) exec = PE3D_EXEC_PERSISTENT;
     p->last_exec = exec;
     const int unitsA = (p->Nt + p->NG - 1) / p->NG;
-    const size_t sA = smemA_bytes<C>(p->NG, p->ldz, p->T);
-    const size_t sB = smemB_bytes<C>(p->rowsB, p->TZ, p->NtP);
     const KernelTable<C>& kt = kernels<C>();
     const int ca = chunk_class(p->L), cb = chunk_class(p->Lt);
     if (steps == 0) { p->last_launches = 0; return PE3D_OK; }
     if (p->timing) PE3D_CUDA(cudaEventRecord(p->ev0, p->stream));
     if (exec == PE3D_EXEC_PERSISTENT) {
         int grid = 0;
-        int rc = persistent_grid<C>(p, &grid);
+        int rc = persistent_grid<C>(p, &A.sp, &grid);
         if (rc) return rc;
         PE3D_CUDA(cudaMemsetAsync(p->bar, 0, sizeof(unsigned), p->stream));
         A.j0 = 0; A.j1 = steps;
         void* args[] = {&A};
-        PE3D_CUDA(cudaLaunchCooperativeKernel(kt.persist[ca][cb], dim3(grid), dim3(NT), args,
-                                              smem_persistent<C>(p), p->stream));
+        PE3D_CUDA(cudaLaunchCooperativeKernel(kt.persist[ca][cb], dim3(grid), dim3(NT), args, A.sp.total,
+                                              p->stream));
         p->last_grid = grid;
         p->last_launches = 1;
         if (p->timing) PE3D_CUDA(cudaEventRecord(p->ev1, p->stream));
@@ -269,10 +298,11 @@ int run_steps(pe3d_plan_s* p, MarchArgs<C>& A, int steps) {
         PE3D_CUDA(cudaStreamBeginCapture(ls, cudaStreamCaptureModeThreadLocal));
     }
     cudaError_t e = cudaSuccess;
+    A.sp = single_unit_plan<C>(p);
     for (int j = 0; j < steps && e == cudaSuccess; ++j) {
         void* args[] = {&A, &j};
-        e = cudaLaunchKernel(kt.A[ca], dim3(unitsA), dim3(NT), args, sA, ls);
-        if (e == cudaSuccess) e = cudaLaunchKernel(kt.B[cb], dim3(p->tiles), dim3(NT), args, sB, ls);
+        e = cudaLaunchKernel(kt.A[ca], dim3(unitsA), dim3(NT), args, A.sp.total, ls);
+        if (e == cudaSuccess) e = cudaLaunchKernel(kt.B[cb], dim3(p->tiles), dim3(NT), args, A.sp.total, ls);
     }
     if (exec == PE3D_EXEC_GRAPH) {
         cudaGraph_t graph = nullptr;

@@ -48,6 +48,9 @@ __global__ void k_static_slice_table(SliceRanges sr, int steps, double r0, doubl
 
 inline size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
+template <typename C>
+constexpr bool precision_is_fp32() { return sizeof(C) == 8; }
+
 // Device address of the scratch array on the current device (looked up once).
 int scratch_address(void** out) {
     int dev = 0;
@@ -149,13 +152,15 @@ int run_static(pe3d_plan_s& p, const pe3d_host::StaticKernels& kt, unsigned char
         A.bar = reinterpret_cast<unsigned*>(base + cv.bar); A.status = status;
         A.j0 = 0; A.j1 = steps;
         const void* fn = kt.persist[chunk_class(p.L)][chunk_class(p.Lt)];
-        const size_t smem = std::max(smemA_bytes<C>(p.NG, p.ldz, p.T), smemB_bytes<C>(p.rowsB, p.TZ, p.NtP));
+        int grid = 0;
+        if (precision_is_fp32<C>()) pe3d_host::persistent_config_f32(&p, &A.sp, &grid);
+        else pe3d_host::persistent_config_f64(&p, &A.sp, &grid);
+        const size_t smem = A.sp.total;
         int nb = 0;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, NT, smem)) != cudaSuccess)
             return cuda_fail(e, "occupancy");
         if (nb < 1) return pe3d_host::fail(PE3D_ERR_ARG, "persistent kernel does not fit on an SM");
-        const int unitsA = (p.Nt + p.NG - 1) / p.NG;
-        const int grid = std::min(nb * p.num_sms, std::max(unitsA, p.tiles));
+        grid = std::min(grid, nb * p.num_sms);
         void* args[] = {&A};
         if ((e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(NT), args, smem, st)) != cudaSuccess)
             return cuda_fail(e, "persistent march");
@@ -242,7 +247,7 @@ extern "C" int pe3d_march_static(int Nz, int Ntheta, double dz, double dtheta, d
     }
     unsigned char* b = static_cast<unsigned char*>(base);
     p.v = b + cv.v;
-    if ((rc = encode_tmap_v(&p))) return rc;
+    if ((rc = encode_tmaps(&p))) return rc;
     StaticKernels kt;
     if ((rc = precision == PE3D_FP32 ? static_kernels_f32(&kt) : static_kernels_f64(&kt))) return rc;
     SliceRanges sr;

@@ -1,12 +1,12 @@
 """Sub-step tracing of the range march (one GPU).
 
 Builds a copy of the library with -DPE3D_TRACE into _build/trace/ and marches
-the walled 100 Hz grid for a few steps.  The trace build makes thread 0 of
-every CTA record clock64() at each sub-step of the two phases and around the
-grid barriers.  Prints the median and maximum SM cycles of each sub-step over
-the CTAs:
+one workload for a few steps.  In the trace build, thread 0 of every CTA adds
+the SM cycles since its previous mark to the slot of the interval that ends
+there, over every unit and range step.  Prints, per interval, the mean over
+the CTAs of the cycles spent per range step (their sum is the step time):
 
-    python -m paper_1711_00005_gb300.trace [--steps 20] [--exec 3]
+    python -m paper_1711_00005_gb300.trace [--workload medium-100Hz] [--steps 20] [--exec 3]
 
 The traced library is separate from libpe3d.so and is never loaded by the
 library's users.
@@ -27,8 +27,13 @@ from . import build as _build
 TRACE_DIR = os.path.join(_build.BUILD, "trace")
 TRACE_LIB = os.path.join(TRACE_DIR, "libpe3d_trace.so")
 SLOTS = 24
-NAMES_A = ["tma_wait", "F1", "scan1", "F2+B1", "scan2", "B2+sync", "store"]
-NAMES_B = ["tma_wait", "F1", "scan1", "F2+B1", "scan2", "B2+sync", "epilogue"]
+# interval ending at each mark (slot number -> name)
+NAMES = {
+    0: "A: before unit", 1: "A: TMA wait", 2: "A: F1", 3: "A: scan1", 4: "A: F2+B1", 5: "A: scan2",
+    6: "A: B2+sync", 7: "A: store v", 16: "A: after units", 17: "barrier 1",
+    8: "B: before tile", 9: "B: TMA wait", 10: "B: F1", 11: "B: scan1", 12: "B: F2+B1", 13: "B: scan2",
+    14: "B: B2+SM+sync", 15: "B: epilogue", 18: "B: after tiles", 19: "barrier 2",
+}
 
 
 def build_traced() -> str:
@@ -51,8 +56,10 @@ def build_traced() -> str:
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--workload", choices=["medium-100Hz", "periodic-200Hz"], default="medium-100Hz")
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--exec", type=int, default=3, help="1 stream, 3 persistent")
+    ap.add_argument("--autotune-steps", type=int, default=100, help="choose the layout as bench.py does (0: off)")
     a = ap.parse_args(argv)
     import torch
 
@@ -62,32 +69,31 @@ def main(argv=None):
 
     L = P.load_library(build_traced())
     L.pe3d_trace_read.argtypes = [ctypes.c_void_p, ctypes.c_size_t]
-    wl = workloads.config2(steps=a.steps)
+    make = workloads.config2 if a.workload == "medium-100Hz" else workloads.config3
+    wl = make(steps=a.steps)
     g = wl.grid
     plan = P.Plan.for_grid(g, fp32=True, exec_mode=a.exec)
     plan.set_medium(torch.from_numpy(wl.n2).cuda(), wl.slice_r)
+    if a.autotune_steps > 0:
+        P.pe3d_autotune(plan.h, g.r0, min(a.autotune_steps, g.steps))
     u0 = torch.from_numpy(wl.u0.astype(np.complex64)).cuda()
-    plan.march(u0, g.r0, g.steps, g.steps)
-    torch.cuda.synchronize()
     buf = np.zeros((4096, SLOTS), np.int64)
+    plan.march(u0, g.r0, g.steps, g.steps)          # warm-up, then clear the counters
+    L.pe3d_trace_read(buf.ctypes.data, buf.nbytes)
+    plan.march(u0, g.r0, g.steps, g.steps)
     L.pe3d_trace_read(buf.ctypes.data, buf.nbytes)
     inf = plan.info()
-    ng = 256 // inf["zthreads"]
-    nA = (g.Ntheta + ng - 1) // ng
-    nB = (g.Nz + inf["ttile"] - 1) // inf["ttile"]
-    A, B = buf[:nA, 0:8], buf[:nB, 8:16]
-    dA, dB = np.diff(A, axis=1), np.diff(B, axis=1)
-    print("layout", {k: inf[k] for k in ("ldz", "zthreads", "zchunk", "ttile", "tchunk", "grid")})
-    print("depth phase (cycles, median/max):",
-          {n: (int(np.median(dA[:, i])), int(dA[:, i].max())) for i, n in enumerate(NAMES_A)})
-    print("azimuth phase (cycles, median/max):",
-          {n: (int(np.median(dB[:, i])), int(dB[:, i].max())) for i, n in enumerate(NAMES_B)})
-    if a.exec == 3:
-        G = inf["grid"]
-        Bb = buf[:G, 16:20]
-        print("grid barriers (cycles, median/max): after depth phase", int(np.median(Bb[:, 1] - Bb[:, 0])),
-              int((Bb[:, 1] - Bb[:, 0]).max()), "; after azimuth phase", int(np.median(Bb[:, 3] - Bb[:, 2])),
-              int((Bb[:, 3] - Bb[:, 2]).max()))
+    G = inf["grid"] if a.exec == 3 else 4096
+    rows = buf[:G]
+    rows = rows[rows.sum(axis=1) != 0]
+    print("workload", g.name, "layout", {k: inf[k] for k in ("ldz", "zthreads", "zchunk", "ttile", "tchunk", "grid")})
+    print(f"{'interval':18s} {'mean':>8s} {'max':>8s}   (SM cycles per range step, over {len(rows)} CTAs)")
+    tot = 0.0
+    for s_, name in NAMES.items():
+        v = rows[:, s_] / g.steps
+        tot += v.mean()
+        print(f"{name:18s} {v.mean():8.0f} {v.max():8.0f}")
+    print(f"{'step total':18s} {tot:8.0f}")
     plan.close()
 
 
