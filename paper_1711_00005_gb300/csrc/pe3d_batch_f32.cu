@@ -14,3 +14,15 @@ int serve_tick_f32(pe3d_plan_s* owner, pe3d::MarchArgs<float2>* descs, int n, in
     return serve_tick<float2>(owner, descs, n, nsteps);
 }
 }  // namespace pe3d_host
+
+#ifdef PE3D_TRACE
+// tracing builds only: the batched kernel's accumulated sub-step cycles
+// (this translation unit's copy of the trace array), then clear them
+extern "C" int pe3d_trace_read_batched(void* host, size_t bytes) {
+    PE3D_CUDA(cudaDeviceSynchronize());
+    PE3D_CUDA(cudaMemcpyFromSymbol(host, pe3d::pe3d_trace, bytes));
+    static long long zeros[4096 * pe3d::TRACE_SLOTS];
+    PE3D_CUDA(cudaMemcpyToSymbol(pe3d::pe3d_trace, zeros, sizeof(zeros)));
+    return PE3D_OK;
+}
+#endif

@@ -864,6 +864,7 @@ __global__ void __launch_bounds__(NT, 2) k_march_batched(const MarchArgs<C>* __r
     for (int i = threadIdx.x; i <= n; i += NT) { s_pa[i] = pref[i]; s_pb[i] = pref[n + 1 + i]; }
     for (int i = threadIdx.x; i < n; i += NT) { s_j0[i] = D[i].j0; s_j1[i] = D[i].j1; }
     init_mbarriers(smem);
+    PE3D_TRACE_INIT();
     uint32_t par = 0;
     const int G = gridDim.x;
     const int nbufA = D[0].sp.nbufA, nbufB = D[0].sp.nbufB;   // one shared-memory plan for the batch
@@ -902,7 +903,9 @@ __global__ void __launch_bounds__(NT, 2) k_march_batched(const MarchArgs<C>* __r
             },
             [&](int u) { return activeA(u + G); });
         if (!ok) PE3D_ABORT();
+        PE3D_MARK(16);
         if (!grid_barrier(bar, (++nb) * G, status)) PE3D_ABORT();
+        PE3D_MARK(17);
         const int fb = activeB(blockIdx.x);
         if (fb >= 0 && threadIdx.x == 0) loadUB(fb, 0);
         ok = unit_pipeline(
@@ -913,7 +916,9 @@ __global__ void __launch_bounds__(NT, 2) k_march_batched(const MarchArgs<C>* __r
             },
             [&](int u) { return activeB(u + G); });
         if (!ok) PE3D_ABORT();
+        PE3D_MARK(18);
         if (!grid_barrier(bar, (++nb) * G, status)) PE3D_ABORT();
+        PE3D_MARK(19);
     }
 }
 

@@ -56,7 +56,9 @@ def build_traced() -> str:
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("--workload", choices=["medium-100Hz", "periodic-200Hz"], default="medium-100Hz")
+    ap.add_argument("--workload", choices=["medium-100Hz", "periodic-200Hz", "batched-25-400Hz"],
+                    default="medium-100Hz")
+    ap.add_argument("--members", type=int, default=32, help="batched: the highest-frequency members only")
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--exec", type=int, default=3, help="1 stream, 3 persistent")
     ap.add_argument("--autotune-steps", type=int, default=100, help="choose the layout as bench.py does (0: off)")
@@ -69,6 +71,8 @@ def main(argv=None):
 
     L = P.load_library(build_traced())
     L.pe3d_trace_read.argtypes = [ctypes.c_void_p, ctypes.c_size_t]
+    if a.workload == "batched-25-400Hz":
+        return trace_batched(P, L, workloads, a)
     make = workloads.config2 if a.workload == "medium-100Hz" else workloads.config3
     wl = make(steps=a.steps)
     g = wl.grid
@@ -87,14 +91,51 @@ def main(argv=None):
     rows = buf[:G]
     rows = rows[rows.sum(axis=1) != 0]
     print("workload", g.name, "layout", {k: inf[k] for k in ("ldz", "zthreads", "zchunk", "ttile", "tchunk", "grid")})
+    report(rows, g.steps)
+    plan.close()
+
+
+def report(rows, steps):
     print(f"{'interval':18s} {'mean':>8s} {'max':>8s}   (SM cycles per range step, over {len(rows)} CTAs)")
     tot = 0.0
     for s_, name in NAMES.items():
-        v = rows[:, s_] / g.steps
+        v = rows[:, s_] / steps
         tot += v.mean()
         print(f"{name:18s} {v.mean():8.0f} {v.max():8.0f}")
     print(f"{'step total':18s} {tot:8.0f}")
-    plan.close()
+
+
+def trace_batched(P, L, workloads, a):
+    """The batched launch of the highest-frequency members, all marched a.steps steps."""
+    import torch
+    grids = workloads.config4_grids()[-a.members:]
+    for g in grids:
+        g.steps = a.steps
+        g.stride = g.steps
+    wls = [workloads.config4_member(g) for g in grids]
+    stream = torch.cuda.Stream()
+    plans, u0s, outs = [], [], []
+    for wl in wls:
+        g = wl.grid
+        h = P.pe3d_plan(g.Nz, g.Ntheta, g.dz, g.dtheta, g.dr, g.k0, P.PE3D_WALLED, P.PE3D_FP32, stream)
+        P.pe3d_set_medium(h, torch.from_numpy(wl.n2).cuda(), wl.slice_r)
+        plans.append(h)
+        u0s.append(torch.from_numpy(wl.u0.astype(np.complex64)).cuda())
+        outs.append(torch.empty((1, g.Ntheta, g.Nz), dtype=torch.complex64, device="cuda"))
+    buf = np.zeros((4096, SLOTS), np.int64)
+    L.pe3d_trace_read_batched.argtypes = [ctypes.c_void_p, ctypes.c_size_t]
+    for _ in range(2):    # warm-up, then the traced launch
+        L.pe3d_trace_read_batched(buf.ctypes.data, buf.nbytes)
+        P.pe3d_march_batched(plans, u0s, [g.r0 for g in grids], [g.steps for g in grids],
+                             [g.stride for g in grids], outs)
+    L.pe3d_trace_read_batched(buf.ctypes.data, buf.nbytes)
+    inf = P.pe3d_plan_info(plans[0])
+    print("workload batched", len(grids), "members", [(g.Nz, g.Ntheta) for g in grids[:2]], "...",
+          "grid", inf["grid"])
+    rows = buf[:inf["grid"]]
+    report(rows[rows.sum(axis=1) != 0], a.steps)
+    for h in plans:
+        P.pe3d_destroy(h)
 
 
 if __name__ == "__main__":
