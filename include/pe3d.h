@@ -74,6 +74,14 @@ extern "C" {
 #define PE3D_OPT_TTILE     3    /* depths per azimuth-solve tile: 8, 16 or 32        */
 #define PE3D_OPT_RC_EVERY  4    /* FP64 residual correction every K steps (0 = off)  */
 #define PE3D_OPT_TIMING    5    /* 1: time the range-step kernels with CUDA events   */
+#define PE3D_OPT_OUTPUT    6    /* what pe3d_march stores: one of PE3D_OUT_*          */
+
+/* stored quantity (pe3d_set_option PE3D_OPT_OUTPUT), Fig. 2 lines 10 and 13 */
+#define PE3D_OUT_FIELD     0    /* the envelope u (default)                          */
+#define PE3D_OUT_PRESSURE  1    /* p = u H0^(1)(k0 r), the Hankel factor of the split
+                                   p = u w(r) (Sec. 2, Fig. 2 line 10); complex      */
+#define PE3D_OUT_TL        2    /* transmission loss -20 log10 |p| in dB (Fig. 2
+                                   line 13, Fig. 5); real                            */
 
 typedef struct pe3d_plan_s *pe3d_plan_t;
 
@@ -115,7 +123,11 @@ int pe3d_set_medium(pe3d_plan_t plan, const void *n2, const double *slice_r, int
  *   steps     number of range steps (>= 0)
  *   out_stride  after step j the field is stored when (j+1) % out_stride == 0
  *   out       [steps / out_stride][Ntheta][Nz] complex (plan precision),
- *             host or device; may be NULL when steps / out_stride == 0
+ *             host or device; may be NULL when steps / out_stride == 0.
+ *             With PE3D_OPT_OUTPUT = PE3D_OUT_PRESSURE each snapshot holds
+ *             p = u H0^(1)(k0 r) at its range r = r0 + (j+1) dr; with
+ *             PE3D_OUT_TL it holds -20 log10 |p| as real numbers of the plan
+ *             precision ([steps / out_stride][Ntheta][Nz] float or double).
  * Errors: PE3D_ERR_ARG, PE3D_ERR_STATE (no medium), PE3D_ERR_SINGULAR,
  * PE3D_ERR_TIMEOUT, PE3D_ERR_OOM, PE3D_ERR_CUDA. */
 int pe3d_march(pe3d_plan_t plan, const void *u0, int u0_on_device, double r0, int steps,

@@ -10,7 +10,9 @@ and cyclic solvers are pinned to LAPACK via numpy.linalg.solve and to the
 circulant FFT solution; the step is pinned to a dense LU solve of the printed
 Eq. 4 on tiny grids, to the closed-form discrete eigenmode multipliers, to
 exact norm conservation, to reversibility, to the theta-uniform reduction and
-to mirror symmetry (tests/test_oracle_pins.py).  No value printed in the
+to mirror symmetry (tests/test_oracle_pins.py); the pressure/TL output to
+Hankel's expansion and tabulated Bessel zeros (tests/test_oracle_output.py).
+No value printed in the
 paper pins it: the paper prints no field values (parity to the paper's own
 outputs is unpinned).
 """
@@ -127,3 +129,34 @@ def load() -> OracleLib:
 def march_workload(wl, **kw):
     """Oracle march of a workloads.Workload."""
     return load().march(wl.grid, wl.n2, wl.slice_r, wl.u0, **kw)
+
+
+# ---------------------------------------------------------------------------
+# pressure and transmission loss (Sec. 2: p = u w(r) with w the Hankel
+# function H0^(1)(k0 r); Fig. 2 line 10 forms p every step, line 13 writes TL)
+# ---------------------------------------------------------------------------
+
+def hankel0(x):
+    """H0^(1)(x) = J0(x) + i Y0(x), the library routine (scipy.special.hankel1)
+    serving as this step.  Pinned in tests/test_oracle_output.py against
+    Hankel's large-argument expansion and the tabulated zeros of J0 and Y0."""
+    from scipy.special import hankel1
+    return hankel1(0, np.asarray(x, dtype=np.float64))
+
+
+def snapshot_ranges(r0, dr, steps, stride):
+    """Ranges of the stored snapshots: after step j the march is at
+    r0 + (j+1) dr, and snapshot s (1-based) is taken after step s*stride - 1."""
+    n_out = steps // stride
+    return r0 + dr * stride * np.arange(1, n_out + 1, dtype=np.float64)
+
+
+def pressure(u_snaps, ranges, k0):
+    """p = u H0^(1)(k0 r) for snapshots u_snaps[s] taken at ranges[s]."""
+    h = hankel0(k0 * np.asarray(ranges, dtype=np.float64))
+    return np.asarray(u_snaps, dtype=np.complex128) * h[:, None, None]
+
+
+def transmission_loss(p):
+    """TL = -20 log10 |p| in dB (Fig. 2 line 13, Fig. 5)."""
+    return -20.0 * np.log10(np.abs(p))

@@ -42,6 +42,10 @@ PE3D_OPT_ZTHREADS = 2
 PE3D_OPT_TTILE = 3
 PE3D_OPT_RC_EVERY = 4
 PE3D_OPT_TIMING = 5
+PE3D_OPT_OUTPUT = 6
+PE3D_OUT_FIELD = 0
+PE3D_OUT_PRESSURE = 1
+PE3D_OUT_TL = 2
 
 PE3D_REQ_PENDING = 0
 PE3D_REQ_RUNNING = 1
@@ -279,7 +283,7 @@ class Plan:
     """Owning wrapper of a pe3d plan; fields in and out as torch tensors."""
 
     def __init__(self, Nz, Ntheta, dz, dtheta, dr, k0, *, periodic=False, fp32=False, stream=None,
-                 exec_mode=None, zthreads=None, ttile=None):
+                 exec_mode=None, zthreads=None, ttile=None, output=None):
         import torch
         self.torch = torch
         if stream is None:
@@ -296,6 +300,9 @@ class Plan:
             pe3d_set_option(self.h, PE3D_OPT_ZTHREADS, zthreads)
         if ttile is not None:
             pe3d_set_option(self.h, PE3D_OPT_TTILE, ttile)
+        self.output = PE3D_OUT_FIELD if output is None else output
+        if output is not None:
+            pe3d_set_option(self.h, PE3D_OPT_OUTPUT, output)
 
     @classmethod
     def for_grid(cls, grid, **kw):
@@ -308,7 +315,10 @@ class Plan:
         torch = self.torch
         n_out = steps // stride
         if out is None:
-            out = torch.empty((n_out, self.Ntheta, self.Nz), dtype=self.cdtype, device="cuda")
+            dt = self.cdtype
+            if self.output == PE3D_OUT_TL:     # transmission loss is real
+                dt = torch.float32 if self.fp32 else torch.float64
+            out = torch.empty((n_out, self.Ntheta, self.Nz), dtype=dt, device="cuda")
         pe3d_march(self.h, u0, r0, steps, stride, out if n_out > 0 else None)
         return out
 

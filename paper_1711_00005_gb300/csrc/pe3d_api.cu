@@ -208,6 +208,10 @@ int pe3d_set_option(pe3d_plan_t p, int option, int value) {
             }
             p->timing = value ? 1 : 0;
             return PE3D_OK;
+        case PE3D_OPT_OUTPUT:
+            if (value < PE3D_OUT_FIELD || value > PE3D_OUT_TL) return fail(PE3D_ERR_ARG, "unknown output");
+            p->out_mode = value;
+            return PE3D_OK;
         case PE3D_OPT_RC_EVERY:
             if (value < 0) return fail(PE3D_ERR_ARG, "RC_EVERY must be >= 0");
             if (value > 0 && p->precision != PE3D_FP32) return fail(PE3D_ERR_ARG, "residual correction is for FP32 plans");
@@ -227,6 +231,7 @@ int pe3d_get_option(pe3d_plan_t p, int option, int* value) {
         case PE3D_OPT_TTILE: *value = p->ldz ? p->TZ : p->ttile; return PE3D_OK;
         case PE3D_OPT_RC_EVERY: *value = p->rc_every; return PE3D_OK;
         case PE3D_OPT_TIMING: *value = p->timing; return PE3D_OK;
+        case PE3D_OPT_OUTPUT: *value = p->out_mode; return PE3D_OK;
         default: return fail(PE3D_ERR_ARG, "unknown option");
     }
 }
@@ -285,6 +290,8 @@ int pe3d_march(pe3d_plan_t p, const void* u0, int u0_on_device, double r0, int s
     if (n_out > 0 && out_on_device && !on_device_ptr(out)) return fail(PE3D_ERR_ARG, "out is not device memory");
     const size_t eb = elem_bytes(p);
     const size_t fbytes = (size_t)p->Nt * p->Nz * eb;
+    // a snapshot is complex, or real (half the bytes) for transmission loss
+    const size_t sbytes = p->out_mode == PE3D_OUT_TL ? fbytes / 2 : fbytes;
     int rc;
     const void* u0_dev = u0;
     if (!u0_on_device) {
@@ -297,7 +304,7 @@ int pe3d_march(pe3d_plan_t p, const void* u0, int u0_on_device, double r0, int s
         if (out_on_device) {
             snap = out;
         } else {
-            const size_t need = (size_t)n_out * fbytes;
+            const size_t need = (size_t)n_out * sbytes;
             if (need > p->outstage_bytes) {
                 dev_free(p, &p->outstage, p->outstage_bytes);
                 p->outstage_bytes = 0;
@@ -312,7 +319,7 @@ int pe3d_march(pe3d_plan_t p, const void* u0, int u0_on_device, double r0, int s
                                    : march_f64(p, u0_dev, r0, steps, out_stride, snap, p->Nz);
     if (rc) return rc;
     if (n_out > 0 && !out_on_device)
-        PE3D_CUDA(cudaMemcpyAsync(out, snap, (size_t)n_out * fbytes, cudaMemcpyDeviceToHost, p->stream));
+        PE3D_CUDA(cudaMemcpyAsync(out, snap, (size_t)n_out * sbytes, cudaMemcpyDeviceToHost, p->stream));
     rc = read_status(p);
     if (rc) return rc;
     p->last_kernel_ns = 0;

@@ -119,7 +119,7 @@ int batched_impl(int n, pe3d_plan_s* const* plans, const void* const* u0, const 
     int nsteps = 0;
     for (int i = 0; i < n; ++i) {
         pe3d_plan_s* p = plans[i];
-        if (steps[i] > 0 && (rc = step_setup<C>(p, r0[i], steps[i]))) return rc;
+        if (steps[i] > 0 && (rc = step_setup<C>(p, r0[i], steps[i], stride[i]))) return rc;
         if ((rc = launch_prologue<C>(p, u0[i], r0[i]))) return rc;
         fill_args<C>(p, descs[i]);
         descs[i].snap = reinterpret_cast<C*>(out[i]);
@@ -150,7 +150,7 @@ template <typename C>
 int serve_begin(pe3d_plan_s* p, const void* u0_dev, double r0, int steps, int stride, void* snap_dev,
                 MarchArgs<C>* desc) {
     int rc;
-    if (steps > 0 && (rc = step_setup<C>(p, r0, steps))) return rc;
+    if (steps > 0 && (rc = step_setup<C>(p, r0, steps, stride))) return rc;
     if ((rc = launch_prologue<C>(p, u0_dev, r0))) return rc;
     fill_args<C>(p, *desc);
     desc->snap = reinterpret_cast<C*>(snap_dev);

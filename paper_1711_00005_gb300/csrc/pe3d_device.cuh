@@ -261,11 +261,33 @@ struct StepConst {
     double2 xi;      // 1 / (1 + v^T z) (cyclic)
     float2 nbinv32;  // nbinv and qnext rounded once to complex64 (the FP32 march
     float2 qnext32;  // reads these instead of converting per thread)
+    double2 hk;      // H0^(1)(k0 r*) = J0 + i Y0 at this step's range: p = u hk
+    float2 hk32;     // (Fig. 2 line 10), and its complex64 copy
+    float2 pad_;
 };
 // the step constants in the march type
 __device__ __forceinline__ float2 step_nbinv(const StepConst* s, float2) { return s->nbinv32; }
 __device__ __forceinline__ double2 step_nbinv(const StepConst* s, double2) { return s->nbinv; }
 __device__ __forceinline__ float2 step_qnext(const StepConst* s, float2) { return s->qnext32; }
 __device__ __forceinline__ double2 step_qnext(const StepConst* s, double2) { return s->qnext; }
+__device__ __forceinline__ float2 step_hankel(const StepConst* s, float2) { return s->hk32; }
+__device__ __forceinline__ double2 step_hankel(const StepConst* s, double2) { return s->hk; }
+
+// what a snapshot stores (PE3D_OUT_*): the field u, the pressure p = u hk, or
+// the transmission loss -20 log10 |p| as a real number at real index e of the
+// snapshot (complex index e for the first two)
+constexpr int OUT_FIELD = 0, OUT_PRESSURE = 1, OUT_TL = 2;
+__device__ __forceinline__ float tl_db(float2 p) { return -20.0f * log10f(hypotf(p.x, p.y)); }
+__device__ __forceinline__ double tl_db(double2 p) { return -20.0 * log10(hypot(p.x, p.y)); }
+template <typename C>
+__device__ __forceinline__ void store_snapshot(void* snap, size_t e, C u, int mode, C hk) {
+    if (mode == OUT_FIELD) {
+        reinterpret_cast<C*>(snap)[e] = u;
+        return;
+    }
+    const C p = cmul(hk, u);
+    if (mode == OUT_PRESSURE) reinterpret_cast<C*>(snap)[e] = p;
+    else reinterpret_cast<typename real_of<C>::type*>(snap)[e] = tl_db(p);
+}
 
 }  // namespace pe3d

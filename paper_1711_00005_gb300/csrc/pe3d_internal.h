@@ -26,6 +26,7 @@ struct pe3d_plan_s {
     int ctas_per_sm = 0;    // persistent march: 1 or 2 (0 = 1); set by the autotuner
     int rc_every = 0;
     int timing = 0;
+    int out_mode = PE3D_OUT_FIELD;   // what the snapshots hold
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaStream_t capture = nullptr;   // private stream for graph capture
     int64_t last_kernel_ns = 0;

@@ -85,8 +85,9 @@ struct MarchArgs {
     const C* zsm;               // [steps][NtP] Sherman-Morrison vector (periodic)
     const StepConst* sc;        // [steps]
     C c1, c2p;                  // v = c1 w + c2p * (scaled depth solution)
-    C* snap;                    // [n_out][Nt][snap_ld] or nullptr
+    C* snap;                    // [n_out][Nt][snap_ld] or nullptr (real for OUT_TL)
     int snap_ld;
+    int out_mode = OUT_FIELD;   // what the snapshots hold (OUT_*)
     int stride;                 // snapshot every `stride` steps
     unsigned* bar;              // grid-barrier counter (persistent launch)
     int* status;
@@ -507,7 +508,6 @@ __device__ bool computeB(const MarchArgs<C>& P, int j, int tile, unsigned char* 
     const bool refine_next = !solve_only && P.rc_every > 0 && (j + 2) % P.rc_every == 0;
     const C q = solve_only ? zero : qn;
     const bool snap = !solve_only && !refine_now && P.snap != nullptr && ((j + 1) % P.stride) == 0;
-    C* snp = snap ? P.snap + (size_t)((j + 1) / P.stride - 1) * Nt * P.snap_ld + p0 + g : nullptr;
     const bool col_ok = p0 + g < P.Nz;
     // neighbours across the chunk edges: row r0-1 and row r0+Lt; the row after
     // Nt-1 is row 0 on a full circle and the zero ghost between walls
@@ -529,9 +529,15 @@ __device__ bool computeB(const MarchArgs<C>& P, int j, int tile, unsigned char* 
         const C wn = refine_now ? vq[i] : cfma(q, lap, vq[i]);
         if (i < Lt && row < Nt) {
             __stcg(wcol + (size_t)i * ldz, wn);
-            if (snap && col_ok) snp[(size_t)row * P.snap_ld] = vq[i];
             if (ucol) __stcg(ucol + (size_t)i * ldz, vq[i]);
         }
+    }
+    if (snap && col_ok) {      // every stride-th step: u, p or TL of the new field
+        const size_t snp = (size_t)((j + 1) / P.stride - 1) * Nt * P.snap_ld + p0 + g;
+        const C hk = P.out_mode != OUT_FIELD ? step_hankel(scp, C{}) : zero;
+#pragma unroll
+        for (int i = 0; i < LB; ++i)
+            if (i < Lt && r0 + i < Nt) store_snapshot(P.snap, snp + (size_t)(r0 + i) * P.snap_ld, vq[i], P.out_mode, hk);
     }
     __syncthreads();                              // the tile is free for the next copy
     PE3D_MARK(15);
@@ -704,7 +710,8 @@ __device__ void combine_phase(const MarchArgs<C>& P, int j) {
     const size_t ld = P.ldz;
     const C q = from64<C>(P.sc[j].qnext);
     const bool snap = P.snap != nullptr && ((j + 1) % P.stride) == 0;
-    C* sp = snap ? P.snap + (size_t)((j + 1) / P.stride - 1) * Nt * P.snap_ld : nullptr;
+    const size_t sp = snap ? (size_t)((j + 1) / P.stride - 1) * Nt * P.snap_ld : 0;
+    const C hk = snap && P.out_mode != OUT_FIELD ? step_hankel(P.sc + j, C{}) : czero<C>();
     const bool keep = P.rc_every > 0 && (j + 2) % P.rc_every == 0;
     const C two = cmake((R)2, (R)0);
     const long long n = (long long)Nt * ld;
@@ -721,7 +728,7 @@ __device__ void combine_phase(const MarchArgs<C>& P, int j) {
             if (m + 1 < Nt) upv = corrected(m + 1); else if (P.periodic) upv = corrected(0);
             if (m > 0) dnv = corrected(m - 1); else if (P.periodic) dnv = corrected(Nt - 1);
             w = cfma(q, csub(cadd(upv, dnv), cmul(two, u)), u);
-            if (snap) sp[(size_t)m * P.snap_ld + l] = u;
+            if (snap) store_snapshot(P.snap, sp + (size_t)m * P.snap_ld + l, u, P.out_mode, hk);
             if (keep) __stcg(P.up + idx, u);
         }
         __stcg(P.w + idx, w);
@@ -979,14 +986,15 @@ __global__ void k_setupA(const double2* __restrict__ n2, int KNt, int Nz, int ld
     if (bad) atomicExch(status, ST_SINGULAR);
 }
 
-// Azimuth systems of every step: thread per step j.  B_j = I - (d/4) Y_j has
+// Azimuth systems of every step: thread per step j (and the Hankel factor of
+// the pressure output on snapshot steps).  B_j = I - (d/4) Y_j has
 // diagonal 1 + d c_j / 2 and off-diagonal e_B = -d c_j / 4, the same for every
 // depth.  Full circle: T = B - u v^T with gamma = -diag, u = (gamma, 0.., e_B),
 // v = (1, 0.., e_B / gamma); z = T^-1 u and xi = 1 / (1 + v.z) are FP64.
 template <typename C>
 __global__ void k_setupB(int steps, int Nt, int NtP, int periodic, double k0, double dr, double dtheta,
                          double r0, C* __restrict__ mB, C* __restrict__ zsm, double2* __restrict__ gscr,
-                         StepConst* __restrict__ sc, int* status) {
+                         StepConst* __restrict__ sc, int* status, int hk_stride) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= steps) return;
     const double kd = k0 * dr;
@@ -1006,6 +1014,12 @@ __global__ void k_setupB(int steps, int Nt, int NtP, int periodic, double k0, do
     out.xi = make_double2(0.0, 0.0);
     out.nbinv32 = from64<float2>(out.nbinv);
     out.qnext32 = from64<float2>(out.qnext);
+    // H0^(1)(k0 r*) (r* > 0) on the steps whose snapshot needs it (every
+    // hk_stride-th step; hk_stride = 0: none)
+    out.hk = (hk_stride > 0 && (j + 1) % hk_stride == 0) ? make_double2(j0(k0 * rs), y0(k0 * rs))
+                                                          : make_double2(0.0, 0.0);
+    out.hk32 = from64<float2>(out.hk);
+    out.pad_ = make_float2(0.f, 0.f);
     C* mrow = mB + (size_t)j * NtP;
     double2 mprev = make_double2(0.0, 0.0);
     bool bad = false;

@@ -137,6 +137,7 @@ void fill_args(pe3d_plan_s* p, MarchArgs<C>& A) {
     A.c1 = from64<C>(c1);
     A.c2p = from64<C>(c2p);
     A.snap = nullptr; A.snap_ld = p->Nz; A.stride = 1;
+    A.out_mode = p->out_mode;
     A.bar = p->bar; A.status = p->status;
     A.j0 = 0; A.j1 = 0;
     A.rc_every = 0;
@@ -238,7 +239,7 @@ int prepare_kernels(const pe3d_plan_s* p) {
 
 // per-step setup (FP64 azimuth pivots and step constants) + the slice table
 template <typename C>
-int step_setup(pe3d_plan_s* p, double r0, int steps) {
+int step_setup(pe3d_plan_s* p, double r0, int steps, int stride) {
     int rc = ensure_steps(p, steps);
     if (rc) return rc;
     std::vector<int> sos(steps);
@@ -247,7 +248,7 @@ int step_setup(pe3d_plan_s* p, double r0, int steps) {
     k_setupB<C><<<(steps + 127) / 128, 128, 0, p->stream>>>(
         steps, p->Nt, p->NtP, p->boundary == PE3D_PERIODIC, p->k0, p->dr, p->dtheta, r0,
         reinterpret_cast<C*>(p->mB), reinterpret_cast<C*>(p->zsm), reinterpret_cast<double2*>(p->gscr),
-        reinterpret_cast<StepConst*>(p->sc), p->status);
+        reinterpret_cast<StepConst*>(p->sc), p->status, p->out_mode != PE3D_OUT_FIELD ? stride : 0);
     PE3D_CUDA(cudaGetLastError());
     return PE3D_OK;
 }
@@ -327,7 +328,7 @@ int march(pe3d_plan_s* p, const void* u0_dev, double r0, int steps, int stride, 
     int rc = prepare_kernels<C>(p);
     if (rc) return rc;
     if (steps > 0) {
-        rc = step_setup<C>(p, r0, steps);
+        rc = step_setup<C>(p, r0, steps, stride);
         if (rc) return rc;
     }
     rc = launch_prologue<C>(p, u0_dev, r0);

@@ -104,7 +104,7 @@ static int estimate_bytes(const pe3d_request& r, size_t* out) {
     const size_t pts = (size_t)r.Ntheta * r.Nz;
     size_t b = 2 * field + (size_t)r.K * pts * 16 + (size_t)r.K * field + pts * es;
     const size_t steps = (size_t)std::max(r.steps, 1);
-    b += steps * tmp.NtP * es * (r.boundary == PE3D_PERIODIC ? 2 : 1) + steps * (64 + 4);
+    b += steps * tmp.NtP * es * (r.boundary == PE3D_PERIODIC ? 2 : 1) + steps * (sizeof(pe3d::StepConst) + 4);
     if (r.boundary == PE3D_PERIODIC) b += 2 * steps * tmp.NtP * 16;
     b += (size_t)(r.steps / r.out_stride) * pts * es;
     *out = b + 4096;

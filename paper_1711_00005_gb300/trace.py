@@ -56,7 +56,7 @@ def build_traced() -> str:
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("--workload", choices=["medium-100Hz", "periodic-200Hz", "batched-25-400Hz"],
+    ap.add_argument("--workload", choices=["medium-100Hz", "periodic-200Hz", "batched-25-400Hz", "served-mix"],
                     default="medium-100Hz")
     ap.add_argument("--members", type=int, default=32, help="batched: the highest-frequency members only")
     ap.add_argument("--steps", type=int, default=20)
@@ -71,7 +71,7 @@ def main(argv=None):
 
     L = P.load_library(build_traced())
     L.pe3d_trace_read.argtypes = [ctypes.c_void_p, ctypes.c_size_t]
-    if a.workload == "batched-25-400Hz":
+    if a.workload in ("batched-25-400Hz", "served-mix"):
         return trace_batched(P, L, workloads, a)
     make = workloads.config2 if a.workload == "medium-100Hz" else workloads.config3
     wl = make(steps=a.steps)
@@ -106,18 +106,27 @@ def report(rows, steps):
 
 
 def trace_batched(P, L, workloads, a):
-    """The batched launch of the highest-frequency members, all marched a.steps steps."""
+    """The batched launch of the highest-frequency members of the 32-frequency
+    batch, or of the first requests of the served stream, all marched a.steps
+    steps."""
     import torch
-    grids = workloads.config4_grids()[-a.members:]
+    if a.workload == "served-mix":
+        reqs = workloads.config5_stream(rate=200.0, duration=3.0, seed=5)[:a.members]
+        grids = [workloads.config5_grid(r, max_steps=a.steps) for r in reqs]
+        wls = [workloads.config5_member(r, g, n_slices=1) for r, g in zip(reqs, grids)]
+    else:
+        grids = workloads.config4_grids()[-a.members:]
+        for g in grids:
+            g.steps = a.steps
+        wls = [workloads.config4_member(g) for g in grids]
     for g in grids:
-        g.steps = a.steps
         g.stride = g.steps
-    wls = [workloads.config4_member(g) for g in grids]
     stream = torch.cuda.Stream()
     plans, u0s, outs = [], [], []
     for wl in wls:
         g = wl.grid
-        h = P.pe3d_plan(g.Nz, g.Ntheta, g.dz, g.dtheta, g.dr, g.k0, P.PE3D_WALLED, P.PE3D_FP32, stream)
+        h = P.pe3d_plan(g.Nz, g.Ntheta, g.dz, g.dtheta, g.dr, g.k0,
+                        P.PE3D_PERIODIC if g.periodic else P.PE3D_WALLED, P.PE3D_FP32, stream)
         P.pe3d_set_medium(h, torch.from_numpy(wl.n2).cuda(), wl.slice_r)
         plans.append(h)
         u0s.append(torch.from_numpy(wl.u0.astype(np.complex64)).cuda())
@@ -130,7 +139,7 @@ def trace_batched(P, L, workloads, a):
                              [g.stride for g in grids], outs)
     L.pe3d_trace_read_batched(buf.ctypes.data, buf.nbytes)
     inf = P.pe3d_plan_info(plans[0])
-    print("workload batched", len(grids), "members", [(g.Nz, g.Ntheta) for g in grids[:2]], "...",
+    print("workload", a.workload, len(grids), "members", [(g.Nz, g.Ntheta) for g in grids[:4]], "...",
           "grid", inf["grid"])
     rows = buf[:inf["grid"]]
     report(rows[rows.sum(axis=1) != 0], a.steps)
