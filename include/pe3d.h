@@ -75,6 +75,11 @@ extern "C" {
 #define PE3D_OPT_RC_EVERY  4    /* FP64 residual correction every K steps (0 = off)  */
 #define PE3D_OPT_TIMING    5    /* 1: time the range-step kernels with CUDA events   */
 #define PE3D_OPT_OUTPUT    6    /* what pe3d_march stores: one of PE3D_OUT_*          */
+#define PE3D_OPT_CTAS      7    /* persistent march: CTAs per SM, 1 or 2 (0: library
+                                   choice, one; pe3d_autotune sets it)               */
+#define PE3D_OPT_Y_MIDPOINT 8   /* 0: Y at r* = r0 + (j+1) dr as Fig. 2 orders it
+                                   (default); 1: Y at the step's midpoint
+                                   r0 + (j + 1/2) dr, the centred variant            */
 
 /* stored quantity (pe3d_set_option PE3D_OPT_OUTPUT), Fig. 2 lines 10 and 13 */
 #define PE3D_OUT_FIELD     0    /* the envelope u (default)                          */

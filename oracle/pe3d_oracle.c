@@ -320,10 +320,13 @@ static int active_slice(const double *slice_r, int K, double r)
 
 /* The range loop of Fig. 2: steps j = 0 .. steps-1 advance r* = r0 + (j+1) dr;
  * after step j, when (j+1) is a multiple of `stride`, the field is stored as
- * out[(j+1)/stride - 1].  n2: [K][Nt][Nz]; u0, out snapshots: [Nt][Nz].     */
+ * out[(j+1)/stride - 1].  n2: [K][Nt][Nz]; u0, out snapshots: [Nt][Nz].
+ * The medium slice is the one active at r*; Y is evaluated at r* too
+ * (Fig. 2 advances r before updating A and B), or, with y_midpoint, at the
+ * step's midpoint r0 + (j + 1/2) dr (the centred variant of the scheme).  */
 int oracle_march(int Nz, int Nt, double dz, double dtheta, double dr, double k0, int periodic,
                  const cplx *n2, const double *slice_r, int K, const cplx *u0, double r0,
-                 int steps, int stride, cplx *out, int nthreads)
+                 int steps, int stride, cplx *out, int nthreads, int y_midpoint)
 {
     if (Nz <= 0 || Nt <= 0 || K <= 0 || steps < 0 || stride <= 0 || r0 <= 0.0) return OR_ERR_ARG;
     size_t npts = (size_t)Nz * Nt;
@@ -333,8 +336,9 @@ int oracle_march(int Nz, int Nt, double dz, double dtheta, double dr, double k0,
     int rc = OR_OK;
     for (int j = 0; j < steps && rc == OR_OK; ++j) {
         double rstar = r0 + (double)(j + 1) * dr;
+        double ry = y_midpoint ? r0 + ((double)j + 0.5) * dr : rstar;
         int k = active_slice(slice_r, K, rstar);
-        rc = oracle_step(Nz, Nt, dz, dtheta, dr, k0, rstar, periodic, n2 + (size_t)k * npts, u, nthreads);
+        rc = oracle_step(Nz, Nt, dz, dtheta, dr, k0, ry, periodic, n2 + (size_t)k * npts, u, nthreads);
         if (rc == OR_OK && (j + 1) % stride == 0)
             memcpy(out + (size_t)((j + 1) / stride - 1) * npts, u, sizeof(cplx) * npts);
     }

@@ -43,6 +43,8 @@ PE3D_OPT_TTILE = 3
 PE3D_OPT_RC_EVERY = 4
 PE3D_OPT_TIMING = 5
 PE3D_OPT_OUTPUT = 6
+PE3D_OPT_CTAS = 7
+PE3D_OPT_Y_MIDPOINT = 8
 PE3D_OUT_FIELD = 0
 PE3D_OUT_PRESSURE = 1
 PE3D_OUT_TL = 2
@@ -283,7 +285,7 @@ class Plan:
     """Owning wrapper of a pe3d plan; fields in and out as torch tensors."""
 
     def __init__(self, Nz, Ntheta, dz, dtheta, dr, k0, *, periodic=False, fp32=False, stream=None,
-                 exec_mode=None, zthreads=None, ttile=None, output=None):
+                 exec_mode=None, zthreads=None, ttile=None, output=None, ctas=None, y_midpoint=None):
         import torch
         self.torch = torch
         if stream is None:
@@ -300,6 +302,10 @@ class Plan:
             pe3d_set_option(self.h, PE3D_OPT_ZTHREADS, zthreads)
         if ttile is not None:
             pe3d_set_option(self.h, PE3D_OPT_TTILE, ttile)
+        if ctas is not None:
+            pe3d_set_option(self.h, PE3D_OPT_CTAS, ctas)
+        if y_midpoint is not None:
+            pe3d_set_option(self.h, PE3D_OPT_Y_MIDPOINT, int(y_midpoint))
         self.output = PE3D_OUT_FIELD if output is None else output
         if output is not None:
             pe3d_set_option(self.h, PE3D_OPT_OUTPUT, output)

@@ -212,6 +212,14 @@ int pe3d_set_option(pe3d_plan_t p, int option, int value) {
             if (value < PE3D_OUT_FIELD || value > PE3D_OUT_TL) return fail(PE3D_ERR_ARG, "unknown output");
             p->out_mode = value;
             return PE3D_OK;
+        case PE3D_OPT_CTAS:
+            if (value < 0 || value > 2) return fail(PE3D_ERR_ARG, "CTAS must be 0, 1 or 2");
+            p->ctas_per_sm = value;
+            return PE3D_OK;
+        case PE3D_OPT_Y_MIDPOINT:
+            if (value != 0 && value != 1) return fail(PE3D_ERR_ARG, "Y_MIDPOINT must be 0 or 1");
+            p->y_mid = value;
+            return PE3D_OK;
         case PE3D_OPT_RC_EVERY:
             if (value < 0) return fail(PE3D_ERR_ARG, "RC_EVERY must be >= 0");
             if (value > 0 && p->precision != PE3D_FP32) return fail(PE3D_ERR_ARG, "residual correction is for FP32 plans");
@@ -232,6 +240,8 @@ int pe3d_get_option(pe3d_plan_t p, int option, int* value) {
         case PE3D_OPT_RC_EVERY: *value = p->rc_every; return PE3D_OK;
         case PE3D_OPT_TIMING: *value = p->timing; return PE3D_OK;
         case PE3D_OPT_OUTPUT: *value = p->out_mode; return PE3D_OK;
+        case PE3D_OPT_CTAS: *value = p->ctas_per_sm; return PE3D_OK;
+        case PE3D_OPT_Y_MIDPOINT: *value = p->y_mid; return PE3D_OK;
         default: return fail(PE3D_ERR_ARG, "unknown option");
     }
 }

@@ -36,8 +36,11 @@ __host__ __device__ __forceinline__ double2 cmake(double r, double i) { return m
 
 template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
 template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+// complex product with its contraction written out (one fma per component),
+// so every kernel that inlines it rounds the same way: the launch modes and
+// batch compositions stay bit-identical
 template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
-    C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+    C r; r.x = fma(a.x, b.x, -(a.y * b.y)); r.y = fma(a.x, b.y, a.y * b.x); return r;
 }
 // a * b + c
 template <typename C> __device__ __forceinline__ C cfma(C a, C b, C c) {
@@ -201,11 +204,6 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// order this thread's generic-proxy view before its later async-proxy accesses
-__device__ __forceinline__ void fence_proxy_async_all() {
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 
 constexpr long long MBAR_SPIN_LIMIT = 1ll << 22;
 

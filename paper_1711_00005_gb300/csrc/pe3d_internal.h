@@ -27,6 +27,7 @@ struct pe3d_plan_s {
     int rc_every = 0;
     int timing = 0;
     int out_mode = PE3D_OUT_FIELD;   // what the snapshots hold
+    int y_mid = 0;                   // Y at the step's midpoint instead of r_{j+1}
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaStream_t capture = nullptr;   // private stream for graph capture
     int64_t last_kernel_ns = 0;

@@ -88,6 +88,7 @@ struct MarchArgs {
     C* snap;                    // [n_out][Nt][snap_ld] or nullptr (real for OUT_TL)
     int snap_ld;
     int out_mode = OUT_FIELD;   // what the snapshots hold (OUT_*)
+    int y_mid = 0;              // Y evaluated at the step's midpoint (else at r_{j+1})
     int stride;                 // snapshot every `stride` steps
     unsigned* bar;              // grid-barrier counter (persistent launch)
     int* status;
@@ -663,7 +664,7 @@ template <typename C>
 __device__ void residual_phase(const MarchArgs<C>& P, int j) {
     const double kd = P.k0 * P.dr;
     const double s = 1.0 / ((P.k0 * P.dz) * (P.k0 * P.dz));
-    const double rs = P.r0 + (double)(j + 1) * P.dr;
+    const double rs = P.r0 + ((double)(j + 1) - (P.y_mid ? 0.5 : 0.0)) * P.dr;   // where Y is evaluated
     const double c = 1.0 / ((P.k0 * rs * P.dtheta) * (P.k0 * rs * P.dtheta));
     const double2 yq = make_double2(0.0, kd * c / 4.0);          // (d/4) c
     const double2 myq = make_double2(0.0, -kd * c / 4.0);
@@ -994,13 +995,15 @@ __global__ void k_setupA(const double2* __restrict__ n2, int KNt, int Nz, int ld
 template <typename C>
 __global__ void k_setupB(int steps, int Nt, int NtP, int periodic, double k0, double dr, double dtheta,
                          double r0, C* __restrict__ mB, C* __restrict__ zsm, double2* __restrict__ gscr,
-                         StepConst* __restrict__ sc, int* status, int hk_stride) {
+                         StepConst* __restrict__ sc, int* status, int hk_stride, int y_mid) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= steps) return;
     const double kd = k0 * dr;
-    const double rs = r0 + (double)(j + 1) * dr;
-    const double c = 1.0 / ((k0 * rs * dtheta) * (k0 * rs * dtheta));
-    const double rn = r0 + (double)(j + 2) * dr;
+    const double rs = r0 + (double)(j + 1) * dr;                 // the field's range after step j
+    const double back = y_mid ? 0.5 : 0.0;                       // Y at r_{j+1}, or at the midpoint
+    const double ry = r0 + ((double)(j + 1) - back) * dr;
+    const double c = 1.0 / ((k0 * ry * dtheta) * (k0 * ry * dtheta));
+    const double rn = r0 + ((double)(j + 2) - back) * dr;
     const double cn = 1.0 / ((k0 * rn * dtheta) * (k0 * rn * dtheta));
     const double2 eB = make_double2(0.0, -kd * c / 4.0);
     const double2 dB = make_double2(1.0, kd * c / 2.0);

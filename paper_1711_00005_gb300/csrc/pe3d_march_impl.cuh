@@ -138,6 +138,7 @@ void fill_args(pe3d_plan_s* p, MarchArgs<C>& A) {
     A.c2p = from64<C>(c2p);
     A.snap = nullptr; A.snap_ld = p->Nz; A.stride = 1;
     A.out_mode = p->out_mode;
+    A.y_mid = p->y_mid;
     A.bar = p->bar; A.status = p->status;
     A.j0 = 0; A.j1 = 0;
     A.rc_every = 0;
@@ -248,14 +249,14 @@ int step_setup(pe3d_plan_s* p, double r0, int steps, int stride) {
     k_setupB<C><<<(steps + 127) / 128, 128, 0, p->stream>>>(
         steps, p->Nt, p->NtP, p->boundary == PE3D_PERIODIC, p->k0, p->dr, p->dtheta, r0,
         reinterpret_cast<C*>(p->mB), reinterpret_cast<C*>(p->zsm), reinterpret_cast<double2*>(p->gscr),
-        reinterpret_cast<StepConst*>(p->sc), p->status, p->out_mode != PE3D_OUT_FIELD ? stride : 0);
+        reinterpret_cast<StepConst*>(p->sc), p->status, p->out_mode != PE3D_OUT_FIELD ? stride : 0, p->y_mid);
     PE3D_CUDA(cudaGetLastError());
     return PE3D_OK;
 }
 
 template <typename C>
 int launch_prologue(pe3d_plan_s* p, const void* u0_dev, double r0) {
-    const double rs = r0 + p->dr;
+    const double rs = r0 + (p->y_mid ? 0.5 : 1.0) * p->dr;     // where step 0 evaluates Y
     const double c0 = 1.0 / ((p->k0 * rs * p->dtheta) * (p->k0 * rs * p->dtheta));
     const double2 q0 = d2(0.0, p->k0 * p->dr * c0 / 4.0);
     const long long n = (long long)p->Nt * p->ldz;

@@ -114,8 +114,9 @@ int run_static(pe3d_plan_s& p, const pe3d_host::StaticKernels& kt, unsigned char
         int Nt = p.Nt, NtP = p.NtP;
         double k0 = p.k0, dr = p.dr, dth = p.dtheta, rr0 = r0;
         int per = periodic, st_steps = steps;
-        int no_hk = 0;     // the allocation-free march stores the field only
-        void* args[] = {&st_steps, &Nt, &NtP, &per, &k0, &dr, &dth, &rr0, &mB, &zsm, &gscr, &sc, &status, &no_hk};
+        int no_hk = 0, y_mid = 0;   // the allocation-free march stores the field, Y at r_{j+1}
+        void* args[] = {&st_steps, &Nt, &NtP, &per, &k0, &dr, &dth, &rr0, &mB, &zsm, &gscr, &sc, &status, &no_hk,
+                        &y_mid};
         if ((e = cudaLaunchKernel(kt.setupB, dim3((steps + 127) / 128), dim3(128), args, 0, st)) != cudaSuccess)
             return cuda_fail(e, "setup of the azimuth systems");
     }

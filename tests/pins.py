@@ -73,15 +73,20 @@ def active_slice(slice_r, r):
     return k
 
 
-def check_dense(lib, periodic: bool, seed: int = 3) -> float:
+def y_range(g, j, y_midpoint):
+    """Range at which Y is evaluated in step j: r_{j+1}, or the midpoint."""
+    return g.r0 + (j + 0.5) * g.dr if y_midpoint else g.r0 + (j + 1) * g.dr
+
+
+def check_dense(lib, periodic: bool, seed: int = 3, y_midpoint: bool = False) -> float:
     wl = workloads.random_case(6, 5, periodic=periodic, K=3, steps=5, seed=seed, stride=1)
     g = wl.grid
-    got = lib.march(g, wl.n2, wl.slice_r, wl.u0)
+    got = lib.march(g, wl.n2, wl.slice_r, wl.u0, y_midpoint=y_midpoint)
     u = wl.u0.copy()
     err = 0.0
     for j in range(g.steps):
         rstar = g.r0 + (j + 1) * g.dr
-        u = dense_step(u, wl.n2[active_slice(wl.slice_r, rstar)], g, rstar)
+        u = dense_step(u, wl.n2[active_slice(wl.slice_r, rstar)], g, y_range(g, j, y_midpoint))
         err = max(err, relerr(got[j], u))
     return err
 
@@ -91,7 +96,7 @@ def check_dense(lib, periodic: bool, seed: int = 3) -> float:
 # --------------------------------------------------------------------------
 
 def check_eigenmodes(lib, periodic: bool, n0sq: float, q: int = 2, p: int = 1,
-                     steps: int = 7) -> float:
+                     steps: int = 7, y_midpoint: bool = False) -> float:
     Nz, Nt = 9, 8
     g = workloads.Grid(Nz=Nz, Ntheta=Nt, dz=3.0, dtheta=(2 * math.pi / Nt) if periodic else 0.05,
                        dr=7.0, k0=0.3, r0=40.0, steps=steps, stride=steps, periodic=periodic)
@@ -106,15 +111,14 @@ def check_eigenmodes(lib, periodic: bool, n0sq: float, q: int = 2, p: int = 1,
         mu_unit = -4.0 * math.sin((p + 1) * math.pi / (2 * (Nt + 1))) ** 2
     u0 = (tmode[:, None] * zmode[None, :]).astype(np.complex128)
     n2 = np.full((1, Nt, Nz), n0sq, np.complex128)
-    got = lib.march(g, n2, np.array([g.r0]), u0)[-1]
+    got = lib.march(g, n2, np.array([g.r0]), u0, y_midpoint=y_midpoint)[-1]
     d = 1j * g.k0 * g.dr
     s = 1.0 / (g.k0 * g.dz) ** 2
     lam = (n0sq - 1.0) - 4.0 * s * math.sin((q + 1) * math.pi / (2 * (Nz + 1))) ** 2
     alpha, beta = 0.25 - d / 4, 0.25 + d / 4
     gain = 1.0 + 0j
     for j in range(steps):
-        rstar = g.r0 + (j + 1) * g.dr
-        c = 1.0 / (g.k0 * rstar * g.dtheta) ** 2
+        c = 1.0 / (g.k0 * y_range(g, j, y_midpoint) * g.dtheta) ** 2
         mu = c * mu_unit
         gain *= (1 + beta * lam) / (1 + alpha * lam) * (1 + d / 4 * mu) / (1 - d / 4 * mu)
     return relerr(got, gain * u0)
@@ -236,6 +240,11 @@ ALL_CHECKS = {
     "eig_walled_09": lambda L: check_eigenmodes(L, False, 0.9),
     "eig_periodic_1": lambda L: check_eigenmodes(L, True, 1.0),
     "eig_periodic_09": lambda L: check_eigenmodes(L, True, 0.9),
+    # the centred variant: Y at the step's midpoint r_j + dr/2
+    "dense_walled_mid": lambda L: check_dense(L, periodic=False, y_midpoint=True),
+    "dense_periodic_mid": lambda L: check_dense(L, periodic=True, y_midpoint=True),
+    "eig_walled_mid": lambda L: check_eigenmodes(L, False, 0.9, y_midpoint=True),
+    "eig_periodic_mid": lambda L: check_eigenmodes(L, True, 0.9, y_midpoint=True),
     "norm_walled": lambda L: check_norm_conservation(L, False),
     "norm_periodic": lambda L: check_norm_conservation(L, True),
     "reverse_walled": lambda L: check_reversibility(L, False),

@@ -5,7 +5,8 @@ Pins (paper Eq. 4-8, Fig. 2):
     theta-dependent media, range-dependent slices (brute force);
   * closed-form per-step multipliers of the discrete sine/Fourier eigenmodes
     in a homogeneous theta-independent medium (pins the X and Y definitions,
-    the sign of delta and the range r* at which operators are evaluated);
+    the sign of delta and the range r* at which operators are evaluated),
+    both at r_{j+1} (Fig. 2) and in the centred variant with Y at r_j + dr/2;
   * exact norm conservation for real theta-independent media;
   * reversibility S(-delta) S(delta) = I for any medium;
   * mirror symmetry and the theta-uniform reduction to an Ntheta = 1 march;
