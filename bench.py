@@ -45,6 +45,10 @@ FALLBACK_HBM_GBS = 6800.0
 # range-step (theta and depth stencils of the RHS, the two elimination sweeps)
 FLOPS_PER_POINT_STEP = 80
 NOMINAL_FP64_GFLOPS = 1250.0
+# per-step depth set-up of an interpolated medium, per grid point and range
+# step: n^2 = (1-t) a + t b (6), d/e + mu = ae n^2 + ce + mu (10), |den|^2 (3),
+# the reciprocal (1) and mu = -conj(den) / |den|^2 (2) -- 22 real FP64 flops
+SETUP_FLOPS_PER_POINT_STEP = 22
 
 
 # ---------------------------------------------------------------------------
@@ -193,16 +197,20 @@ WORKLOADS = {
     "medium-100Hz-fp64": ("fp64", lambda: workloads.config2()),
     "walled-50Hz": ("fp64", lambda: workloads.config1()),
     "periodic-200Hz": ("fp32", lambda: workloads.config3()),
+    "medium-100Hz-interp": ("fp32", lambda: workloads.config2()),
 }
+# workloads whose n^2 is interpolated linearly in range, with the FP64 depth
+# systems set up for every range step
+INTERP_WORKLOADS = {"medium-100Hz-interp"}
 
 
-def oracle_run(wl, steps: int, nthreads: int):
+def oracle_run(wl, steps: int, nthreads: int, interp: bool = False):
     import oracle
     L = oracle.load()
     g = wl.grid
     stride = g.stride if steps % g.stride == 0 else steps
     t = time.perf_counter()
-    out = L.march(g, wl.n2, wl.slice_r, wl.u0, steps=steps, stride=stride, nthreads=nthreads)
+    out = L.march(g, wl.n2, wl.slice_r, wl.u0, steps=steps, stride=stride, nthreads=nthreads, interp=interp)
     return out, time.perf_counter() - t
 
 
@@ -223,11 +231,12 @@ def run_reference(args):
     g = wl.grid
     cores = oracle.default_threads()
     sample_steps = min(g.steps, args.ref_sample_steps)
+    interp = args.workload in INTERP_WORKLOADS
     for _ in range(args.warmup):
-        oracle_run(wl, sample_steps, cores)
+        oracle_run(wl, sample_steps, cores, interp)
     times = []
     for _ in range(args.steps):
-        _, dt = oracle_run(wl, sample_steps, cores)
+        _, dt = oracle_run(wl, sample_steps, cores, interp)
         times.append(dt)
     per = statistics.mean(times)
     value = g.points * sample_steps / per
@@ -235,7 +244,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": g.name, "sample_range_steps": sample_steps, "Nz": g.Nz, "Ntheta": g.Ntheta},
+        "config": {"workload": g.name + ("-interp" if interp else ""), "sample_range_steps": sample_steps,
+                   "Nz": g.Nz, "Ntheta": g.Ntheta},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"first {sample_steps} of {g.steps} range steps of {g.name}, "
                                    f"FP64 C oracle, OpenMP over systems"},
@@ -261,8 +271,11 @@ def run_ours(args):
 
     precision, make = WORKLOADS[args.workload]
     fp32 = precision == "fp32"
+    interp = args.workload in INTERP_WORKLOADS
     wl = make()
     g = wl.grid
+    if interp:
+        g.name += "-interp"
     if args.range_steps:                      # a truncated march (profiling cases)
         g.steps = min(g.steps, args.range_steps)
         g.stride = max(1, min(g.stride, g.steps))
@@ -276,7 +289,7 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         cores = oracle.default_threads()
-        ref, dt = oracle_run(wl, g.steps, cores)
+        ref, dt = oracle_run(wl, g.steps, cores, interp)
         cpu = {"value": g.points * g.steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"the full {g.steps}-step march of {g.name} (FP64 C oracle, OpenMP over "
                          f"systems, {dt:.1f} s)"}
@@ -296,6 +309,8 @@ def run_ours(args):
     P.pe3d_set_option(plan, P.PE3D_OPT_OUTPUT, out_mode)
     if args.rc:
         P.pe3d_set_option(plan, P.PE3D_OPT_RC_EVERY, args.rc)
+    if interp:
+        P.pe3d_set_option(plan, P.PE3D_OPT_MEDIUM_INTERP, 1)
 
     def step():
         P.pe3d_set_medium(plan, n2_dev, wl.slice_r)
@@ -329,13 +344,15 @@ def run_ours(args):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     sampler = ClockSampler(gpu_uuid())
-    kernel_ns = []
+    kernel_ns, setup_ns = [], []
     barrier()
     torch.cuda.synchronize()
     ev0.record(stream)
     for _ in range(args.steps):
         step()
-        kernel_ns.append(P.pe3d_plan_info(plan)["kernel_ns"])
+        inf = P.pe3d_plan_info(plan)
+        kernel_ns.append(inf["kernel_ns"])
+        setup_ns.append(inf["setup_ns"])
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -362,7 +379,7 @@ def run_ours(args):
 
     # plain FP64 GPU march of the same workload, for comparison
     fp64_value = None
-    if fp32 and not args.no_fp64_compare:
+    if fp32 and not args.no_fp64_compare and not interp:
         u064 = torch.from_numpy(wl.u0).to(dev)
         o64 = torch.empty((g.n_out, g.Ntheta, g.Nz), dtype=torch.complex128, device=dev)
         p64 = P.pe3d_plan(g.Nz, g.Ntheta, g.dz, g.dtheta, g.dr, g.k0,
@@ -424,6 +441,9 @@ def run_ours(args):
                 "precision": "complex64 march, FP64 coefficient setup" if fp32 else "complex128",
                 "exec": ["auto", "stream", "graph", "persistent"][info["exec"]],
                 "fp64_residual_correction_every": args.rc or None,
+                "medium": ("n^2 interpolated linearly in range between the slices; FP64 depth systems set up "
+                           "for every range step" if interp else
+                           "piecewise constant in range, FP64 depth systems set up per slice"),
                 "output": {"field": "envelope u", "pressure": "p = u H0(k0 r)",
                            "tl": "-20 log10 |p| (dB)"}[args.output],
                 "layout": {k: info[k] for k in ("ldz", "zthreads", "zchunk", "ttile", "tchunk", "grid")},
@@ -441,6 +461,18 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "clocks": clocks,
         }
+        sns = statistics.mean(setup_ns) if setup_ns and setup_ns[0] > 0 else None
+        if sns:
+            line["setup"] = {"ms": sns / 1e6,
+                             "kernels": ("k_setupA_lerp + k_setupB" if interp else "k_setupB"),
+                             "note": "per-march set-up inside pe3d_march, CUDA events on the plan's stream"}
+            if interp:
+                fl = SETUP_FLOPS_PER_POINT_STEP * point_steps
+                line["setup"].update({"bound": "alu", "achieved": fl / (sns * 1e-9) / 1e12, "unit": "TFLOP/s",
+                                      "peak": NOMINAL_FP64_GFLOPS / 1e3,
+                                      "frac": fl / (sns * 1e-9) / 1e12 / (NOMINAL_FP64_GFLOPS / 1e3),
+                                      "peak_source": "nominal FP64 rate of the profiling recipe",
+                                      "algorithmic_flops_per_launch": fl})
         if fp64_value is not None:
             line["fp64_march"] = {"value": fp64_value, "unit": UNIT, "max_rel_l2_vs_oracle": fp64_err}
         print(json.dumps(line), flush=True)

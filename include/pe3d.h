@@ -80,6 +80,13 @@ extern "C" {
 #define PE3D_OPT_Y_MIDPOINT 8   /* 0: Y at r* = r0 + (j+1) dr as Fig. 2 orders it
                                    (default); 1: Y at the step's midpoint
                                    r0 + (j + 1/2) dr, the centred variant            */
+#define PE3D_OPT_MEDIUM_INTERP 9 /* 0: n^2 piecewise constant in range, slice k for
+                                   R_k <= r* < R_{k+1} (default); 1: n^2 interpolated
+                                   linearly in range between the slices around r*,
+                                   with the depth systems set up in FP64 for every
+                                   range step of each march (Fig. 2 line 7 run per
+                                   step).  Costs Nt*ldz complex of the plan
+                                   precision per step of the longest march. */
 
 /* stored quantity (pe3d_set_option PE3D_OPT_OUTPUT), Fig. 2 lines 10 and 13 */
 #define PE3D_OUT_FIELD     0    /* the envelope u (default)                          */
@@ -115,6 +122,8 @@ int pe3d_get_option(pe3d_plan_t plan, int option, int *value);
  *             host or device memory (n2_on_device)
  *   slice_r   host double [K], ascending ranges: slice k is active for
  *             slice_r[k] <= r* < slice_r[k+1] (slice 0 before slice_r[0])
+ * With PE3D_OPT_MEDIUM_INTERP = 1 the call only uploads and pe3d_march sets
+ * up every step's depth systems from the interpolated n^2.
  * Replaces any previous medium.  Synchronises the plan's stream to report
  * PE3D_ERR_SINGULAR (a depth pivot vanished or is not finite).  Errors:
  * PE3D_ERR_ARG, PE3D_ERR_OOM, PE3D_ERR_SINGULAR, PE3D_ERR_CUDA. */
@@ -147,7 +156,10 @@ int pe3d_destroy(pe3d_plan_t plan);
  * use, [8] device bytes held, [9] kernel launches of the last march,
  * [10] grid size of the last persistent launch, [11] duration of the last
  * march's range-step kernels in ns (CUDA events on the plan's stream; only
- * with PE3D_OPT_TIMING), [12] kernels launched since the plan was created.
+ * with PE3D_OPT_TIMING), [12] kernels launched since the plan was created,
+ * [13] duration of the last march's per-march set-up in ns (azimuth systems
+ * and step constants, and the per-step depth systems of an interpolated
+ * medium; only with PE3D_OPT_TIMING).
  * Returns the count written. */
 int pe3d_plan_info(pe3d_plan_t plan, int64_t *info, int n);
 

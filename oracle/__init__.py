@@ -55,7 +55,7 @@ class OracleLib:
         L.oracle_tridiag_solve.argtypes = [I, P, P, P, P]
         L.oracle_cyclic_solve.argtypes = [I, P, P, P, P]
         L.oracle_step.argtypes = [I, I, D, D, D, D, D, I, P, P, I]
-        L.oracle_march.argtypes = [I, I, D, D, D, D, I, P, P, I, P, D, I, I, P, I, I]
+        L.oracle_march.argtypes = [I, I, D, D, D, D, I, P, P, I, P, D, I, I, P, I, I, I]
         for f in ("oracle_tridiag_solve", "oracle_cyclic_solve", "oracle_step", "oracle_march"):
             getattr(L, f).restype = I
         self.L = L
@@ -93,7 +93,7 @@ class OracleLib:
         return u
 
     def march(self, grid, n2, slice_r, u0, *, steps=None, stride=None, r0=None, nthreads=None,
-              y_midpoint=False):
+              y_midpoint=False, interp=False):
         steps = grid.steps if steps is None else steps
         stride = grid.stride if stride is None else stride
         r0 = grid.r0 if r0 is None else r0
@@ -107,7 +107,7 @@ class OracleLib:
         rc = self.L.oracle_march(Nz, Nt, grid.dz, grid.dtheta, grid.dr, grid.k0, int(grid.periodic),
                                  n2.ctypes.data, slice_r.ctypes.data, len(slice_r), u0.ctypes.data,
                                  float(r0), int(steps), int(stride), out.ctypes.data, int(nthreads),
-                                 int(bool(y_midpoint)))
+                                 int(bool(y_midpoint)), int(bool(interp)))
         if rc:
             raise RuntimeError(f"oracle_march failed ({rc})")
         return out[:n_out]

@@ -29,7 +29,9 @@
  *   - both sides of Eq. 4 use the operators at r* = r_{j+1}: Fig. 2 advances r
  *     before it updates A and B;
  *   - the medium is piecewise constant in range: slice k is active for
- *     R_k <= r* < R_{k+1} (slice 0 before R_0);
+ *     R_k <= r* < R_{k+1} (slice 0 before R_0); or, as the range-dependent
+ *     variant, n^2 is interpolated linearly in range between the slices around
+ *     r* and held constant beyond the first and the last slice;
  *   - the full-circle azimuth system (cyclic) is solved with the Sherman-
  *     Morrison formula around a tridiagonal solve.
  *
@@ -318,30 +320,60 @@ static int active_slice(const double *slice_r, int K, double r)
     return k;
 }
 
+/* n^2 at range r, linear in range between slices: for R_k <= r < R_{k+1},
+ * (1 - t) n2_k + t n2_{k+1} with t = (r - R_k) / (R_{k+1} - R_k); slice 0 before
+ * R_0 and slice K-1 from R_{K-1} on.  out: [Nt][Nz].                      */
+static void interpolated_medium(const cplx *n2, const double *slice_r, int K, size_t npts, double r,
+                                cplx *out)
+{
+    int k = active_slice(slice_r, K, r);
+    if (k + 1 >= K || r < slice_r[k]) {
+        memcpy(out, n2 + (size_t)k * npts, sizeof(cplx) * npts);
+        return;
+    }
+    double t = (r - slice_r[k]) / (slice_r[k + 1] - slice_r[k]);
+    const cplx *a = n2 + (size_t)k * npts, *b = n2 + (size_t)(k + 1) * npts;
+    for (size_t i = 0; i < npts; ++i) out[i] = (1.0 - t) * a[i] + t * b[i];
+}
+
 /* The range loop of Fig. 2: steps j = 0 .. steps-1 advance r* = r0 + (j+1) dr;
  * after step j, when (j+1) is a multiple of `stride`, the field is stored as
  * out[(j+1)/stride - 1].  n2: [K][Nt][Nz]; u0, out snapshots: [Nt][Nz].
  * The medium slice is the one active at r*; Y is evaluated at r* too
  * (Fig. 2 advances r before updating A and B), or, with y_midpoint, at the
- * step's midpoint r0 + (j + 1/2) dr (the centred variant of the scheme).  */
+ * step's midpoint r0 + (j + 1/2) dr (the centred variant of the scheme).
+ * With interp, the medium of step j is n^2 interpolated linearly in range at
+ * r* (interpolated_medium) instead of the active slice.                   */
 int oracle_march(int Nz, int Nt, double dz, double dtheta, double dr, double k0, int periodic,
                  const cplx *n2, const double *slice_r, int K, const cplx *u0, double r0,
-                 int steps, int stride, cplx *out, int nthreads, int y_midpoint)
+                 int steps, int stride, cplx *out, int nthreads, int y_midpoint, int interp)
 {
     if (Nz <= 0 || Nt <= 0 || K <= 0 || steps < 0 || stride <= 0 || r0 <= 0.0) return OR_ERR_ARG;
     size_t npts = (size_t)Nz * Nt;
     cplx *u = (cplx *)malloc(sizeof(cplx) * npts);
-    if (!u) return OR_ERR_OOM;
+    cplx *med = interp ? (cplx *)malloc(sizeof(cplx) * npts) : NULL;
+    if (!u || (interp && !med)) {
+        free(u);
+        free(med);
+        return OR_ERR_OOM;
+    }
     memcpy(u, u0, sizeof(cplx) * npts);
     int rc = OR_OK;
     for (int j = 0; j < steps && rc == OR_OK; ++j) {
         double rstar = r0 + (double)(j + 1) * dr;
         double ry = y_midpoint ? r0 + ((double)j + 0.5) * dr : rstar;
-        int k = active_slice(slice_r, K, rstar);
-        rc = oracle_step(Nz, Nt, dz, dtheta, dr, k0, ry, periodic, n2 + (size_t)k * npts, u, nthreads);
+        const cplx *n2j;
+        if (interp) {
+            interpolated_medium(n2, slice_r, K, npts, rstar, med);
+            n2j = med;
+        } else {
+            n2j = n2 + (size_t)active_slice(slice_r, K, rstar) * npts;
+        }
+        rc = oracle_step(Nz, Nt, dz, dtheta, dr, k0, ry, periodic, n2j, u, nthreads);
         if (rc == OR_OK && (j + 1) % stride == 0)
             memcpy(out + (size_t)((j + 1) / stride - 1) * npts, u, sizeof(cplx) * npts);
     }
     free(u);
+    free(med);
     return rc;
 }

@@ -45,6 +45,7 @@ PE3D_OPT_TIMING = 5
 PE3D_OPT_OUTPUT = 6
 PE3D_OPT_CTAS = 7
 PE3D_OPT_Y_MIDPOINT = 8
+PE3D_OPT_MEDIUM_INTERP = 9
 PE3D_OUT_FIELD = 0
 PE3D_OUT_PRESSURE = 1
 PE3D_OUT_TL = 2
@@ -55,7 +56,7 @@ PE3D_REQ_DONE = 2
 PE3D_REQ_FAILED = 3
 
 INFO_FIELDS = ("Nz", "Ntheta", "ldz", "zthreads", "zchunk", "ttile", "tchunk", "exec", "device_bytes",
-               "launches", "grid", "kernel_ns", "total_launches")
+               "launches", "grid", "kernel_ns", "total_launches", "setup_ns")
 
 
 class PE3DError(RuntimeError):
@@ -285,7 +286,8 @@ class Plan:
     """Owning wrapper of a pe3d plan; fields in and out as torch tensors."""
 
     def __init__(self, Nz, Ntheta, dz, dtheta, dr, k0, *, periodic=False, fp32=False, stream=None,
-                 exec_mode=None, zthreads=None, ttile=None, output=None, ctas=None, y_midpoint=None):
+                 exec_mode=None, zthreads=None, ttile=None, output=None, ctas=None, y_midpoint=None,
+                 interp=None):
         import torch
         self.torch = torch
         if stream is None:
@@ -306,6 +308,8 @@ class Plan:
             pe3d_set_option(self.h, PE3D_OPT_CTAS, ctas)
         if y_midpoint is not None:
             pe3d_set_option(self.h, PE3D_OPT_Y_MIDPOINT, int(y_midpoint))
+        if interp is not None:
+            pe3d_set_option(self.h, PE3D_OPT_MEDIUM_INTERP, int(interp))
         self.output = PE3D_OUT_FIELD if output is None else output
         if output is not None:
             pe3d_set_option(self.h, PE3D_OPT_OUTPUT, output)

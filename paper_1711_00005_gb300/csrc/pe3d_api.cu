@@ -51,17 +51,18 @@ static size_t step_bytes(const pe3d_plan_s* p, int cap, int which) {
         case 1: return p->boundary == PE3D_PERIODIC ? (size_t)cap * p->NtP * eb : 0;      // zsm
         case 2: return p->boundary == PE3D_PERIODIC ? (size_t)2 * cap * p->NtP * 16 : 0;  // gscr
         case 3: return (size_t)cap * sizeof(pe3d::StepConst);                             // sc
-        default: return (size_t)cap * sizeof(int);                                        // slice_of_step
+        case 4: return (size_t)cap * sizeof(int);                                         // slice_of_step
+        default: return (size_t)cap * sizeof(pe3d::MediumStep);                           // lerp
     }
 }
 
 int ensure_steps(pe3d_plan_s* p, int steps) {
     if (steps <= p->step_cap) return PE3D_OK;
     const int cap = std::max(steps, 2 * p->step_cap);
-    void** bufs[5] = {&p->mB, &p->zsm, &p->gscr, &p->sc, (void**)&p->slice_of_step};
-    for (int i = 0; i < 5; ++i) dev_free(p, bufs[i], step_bytes(p, p->step_cap, i));
+    void** bufs[6] = {&p->mB, &p->zsm, &p->gscr, &p->sc, (void**)&p->slice_of_step, &p->lerp};
+    for (int i = 0; i < 6; ++i) dev_free(p, bufs[i], step_bytes(p, p->step_cap, i));
     p->step_cap = 0;
-    for (int i = 0; i < 5; ++i) {
+    for (int i = 0; i < 6; ++i) {
         int rc = dev_alloc(p, bufs[i], step_bytes(p, cap, i));
         if (rc) {
             for (int k = 0; k < i; ++k) dev_free(p, bufs[k], step_bytes(p, cap, k));
@@ -70,6 +71,17 @@ int ensure_steps(pe3d_plan_s* p, int steps) {
     }
     p->step_cap = cap;
     return PE3D_OK;
+}
+
+pe3d::MediumStep medium_step(const std::vector<double>& slice_r, double r) {
+    const int K = (int)slice_r.size();
+    const int k = active_slice(slice_r, r);
+    pe3d::MediumStep m{k, k, 0.0};
+    if (k + 1 < K && r >= slice_r[k]) {
+        m.k1 = k + 1;
+        m.t = (r - slice_r[k]) / (slice_r[k + 1] - slice_r[k]);
+    }
+    return m;
 }
 
 int active_slice(const std::vector<double>& slice_r, double r) {
@@ -181,6 +193,16 @@ int pe3d_plan(int Nz, int Ntheta, double dz, double dtheta, double dr, double k0
     return PE3D_OK;
 }
 
+// FP64 depth multipliers of every slice (Fig. 2 line 7).  An interpolated
+// medium sets its systems up per range step in the march instead.
+static int slice_setup(pe3d_plan_s* p) {
+    if (p->interp) return PE3D_OK;
+    PE3D_CUDA(cudaMemsetAsync(p->status, 0, sizeof(int), p->stream));
+    int rc = p->precision == PE3D_FP32 ? setupA_f32(p) : setupA_f64(p);
+    if (rc) return rc;
+    return read_status(p);
+}
+
 int pe3d_set_option(pe3d_plan_t p, int option, int value) {
     g_err.clear();
     if (!p) return fail(PE3D_ERR_ARG, "plan is NULL");
@@ -205,6 +227,8 @@ int pe3d_set_option(pe3d_plan_t p, int option, int value) {
             if (value && !p->ev0) {
                 PE3D_CUDA(cudaEventCreate(&p->ev0));
                 PE3D_CUDA(cudaEventCreate(&p->ev1));
+                PE3D_CUDA(cudaEventCreate(&p->ev2));
+                PE3D_CUDA(cudaEventCreate(&p->ev3));
             }
             p->timing = value ? 1 : 0;
             return PE3D_OK;
@@ -220,6 +244,14 @@ int pe3d_set_option(pe3d_plan_t p, int option, int value) {
             if (value != 0 && value != 1) return fail(PE3D_ERR_ARG, "Y_MIDPOINT must be 0 or 1");
             p->y_mid = value;
             return PE3D_OK;
+        case PE3D_OPT_MEDIUM_INTERP: {
+            if (value != 0 && value != 1) return fail(PE3D_ERR_ARG, "MEDIUM_INTERP must be 0 or 1");
+            const int was = p->interp;
+            p->interp = value;
+            // the per-slice multipliers are skipped while interpolating: build them on the way back
+            if (was && !value && p->medium_ready) return slice_setup(p);
+            return PE3D_OK;
+        }
         case PE3D_OPT_RC_EVERY:
             if (value < 0) return fail(PE3D_ERR_ARG, "RC_EVERY must be >= 0");
             if (value > 0 && p->precision != PE3D_FP32) return fail(PE3D_ERR_ARG, "residual correction is for FP32 plans");
@@ -242,6 +274,7 @@ int pe3d_get_option(pe3d_plan_t p, int option, int* value) {
         case PE3D_OPT_OUTPUT: *value = p->out_mode; return PE3D_OK;
         case PE3D_OPT_CTAS: *value = p->ctas_per_sm; return PE3D_OK;
         case PE3D_OPT_Y_MIDPOINT: *value = p->y_mid; return PE3D_OK;
+        case PE3D_OPT_MEDIUM_INTERP: *value = p->interp; return PE3D_OK;
         default: return fail(PE3D_ERR_ARG, "unknown option");
     }
 }
@@ -276,11 +309,7 @@ int pe3d_set_medium(pe3d_plan_t p, const void* n2, const double* slice_r, int K,
                               p->stream));
     p->nslices = K;
     p->slice_r.assign(slice_r, slice_r + K);
-    PE3D_CUDA(cudaMemsetAsync(p->status, 0, sizeof(int), p->stream));
-    rc = p->precision == PE3D_FP32 ? setupA_f32(p) : setupA_f64(p);
-    if (rc) return rc;
-    rc = read_status(p);
-    if (rc) return rc;
+    if ((rc = slice_setup(p))) return rc;
     p->medium_ready = true;
     return PE3D_OK;
 }
@@ -333,10 +362,13 @@ int pe3d_march(pe3d_plan_t p, const void* u0, int u0_on_device, double r0, int s
     rc = read_status(p);
     if (rc) return rc;
     p->last_kernel_ns = 0;
+    p->last_setup_ns = 0;
     if (p->timing && steps > 0) {
         float ms = 0.f;
         PE3D_CUDA(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
         p->last_kernel_ns = (int64_t)((double)ms * 1e6);
+        PE3D_CUDA(cudaEventElapsedTime(&ms, p->ev2, p->ev3));
+        p->last_setup_ns = (int64_t)((double)ms * 1e6);
     }
     return PE3D_OK;
 }
@@ -375,9 +407,11 @@ int pe3d_destroy(pe3d_plan_t p) {
     cudaStreamSynchronize(p->stream);
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
+    if (p->ev2) cudaEventDestroy(p->ev2);
+    if (p->ev3) cudaEventDestroy(p->ev3);
     if (p->capture) cudaStreamDestroy(p->capture);
     void** bufs[] = {&p->w, &p->v, &p->u0stage, &p->outstage, &p->n2, &p->mz, &p->mB, &p->zsm, &p->batchbuf, &p->rc_up, &p->rc_ut, &p->rc_db,
-                     &p->gscr, &p->sc, (void**)&p->slice_of_step, (void**)&p->status, (void**)&p->bar};
+                     &p->gscr, &p->sc, (void**)&p->slice_of_step, &p->lerp, &p->mzs, (void**)&p->status, (void**)&p->bar};
     for (void** b : bufs)
         if (*b) { cudaFree(*b); *b = nullptr; }
     delete p;
@@ -388,7 +422,8 @@ int pe3d_plan_info(pe3d_plan_t p, int64_t* info, int n) {
     g_err.clear();
     if (!p || !info || n < 0) return fail(PE3D_ERR_ARG, "bad argument");
     const int64_t vals[] = {p->Nz, p->Nt, p->ldz, p->T, p->L, p->TZ, p->Lt, p->last_exec, p->bytes,
-                            p->last_launches, p->last_grid, p->last_kernel_ns, p->total_launches};
+                            p->last_launches, p->last_grid, p->last_kernel_ns, p->total_launches,
+                            p->last_setup_ns};
     const int cnt = std::min<int>(n, (int)(sizeof(vals) / sizeof(vals[0])));
     for (int i = 0; i < cnt; ++i) info[i] = vals[i];
     return cnt;
@@ -405,8 +440,10 @@ static void drop_layout(pe3d_plan_s* p) {
     dev_free(p, &p->rc_up, fb);
     dev_free(p, &p->rc_ut, fb);
     dev_free(p, &p->rc_db, fb);
-    void** bufs[5] = {&p->mB, &p->zsm, &p->gscr, &p->sc, (void**)&p->slice_of_step};
-    for (int i = 0; i < 5; ++i) {   // per-step tables depend on NtP
+    dev_free(p, &p->mzs, p->mzs_bytes);
+    p->mzs_bytes = 0;
+    void** bufs[6] = {&p->mB, &p->zsm, &p->gscr, &p->sc, (void**)&p->slice_of_step, &p->lerp};
+    for (int i = 0; i < 6; ++i) {   // per-step tables depend on NtP
         if (*bufs[i]) { cudaFree(*bufs[i]); *bufs[i] = nullptr; }
     }
     p->step_cap = 0;
@@ -425,11 +462,7 @@ static int relayout(pe3d_plan_s* p, int T, int TZ) {
     const size_t mb = (size_t)p->nslices * p->Nt * p->ldz * elem_bytes(p);
     if ((rc = dev_alloc(p, &p->mz, mb))) return rc;
     p->mz_bytes = mb;
-    PE3D_CUDA(cudaMemsetAsync(p->status, 0, sizeof(int), p->stream));
-    rc = p->precision == PE3D_FP32 ? setupA_f32(p) : setupA_f64(p);
-    if (rc) return rc;
-    rc = read_status(p);
-    if (rc) return rc;
+    if ((rc = slice_setup(p))) return rc;
     p->medium_ready = true;
     return PE3D_OK;
 }

@@ -263,6 +263,18 @@ struct StepConst {
     float2 hk32;     // (Fig. 2 line 10), and its complex64 copy
     float2 pad_;
 };
+// Medium of one range step when n^2 is interpolated linearly in range:
+// n^2(r*) = (1 - t) n^2_k + t n^2_k1 with R_k <= r* < R_k1, t in [0, 1)
+// (t = 0 and k1 = k outside the slices' span).
+struct MediumStep {
+    int k, k1;
+    double t;
+};
+__host__ __device__ __forceinline__ double2 medium_lerp(double2 a, double2 b, double t) {
+    const double u = 1.0 - t;
+    return make_double2(fma(t, b.x, u * a.x), fma(t, b.y, u * a.y));
+}
+
 // the step constants in the march type
 __device__ __forceinline__ float2 step_nbinv(const StepConst* s, float2) { return s->nbinv32; }
 __device__ __forceinline__ double2 step_nbinv(const StepConst* s, double2) { return s->nbinv; }

@@ -10,6 +10,10 @@
 
 #include "../../include/pe3d.h"
 
+namespace pe3d {
+struct MediumStep;
+}
+
 struct pe3d_plan_s {
     // grid and scheme
     int Nz = 0, Nt = 0;
@@ -28,9 +32,12 @@ struct pe3d_plan_s {
     int timing = 0;
     int out_mode = PE3D_OUT_FIELD;   // what the snapshots hold
     int y_mid = 0;                   // Y at the step's midpoint instead of r_{j+1}
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int interp = 0;                  // n^2 interpolated linearly in range, set up every step
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // around the range-step kernels
+    cudaEvent_t ev2 = nullptr, ev3 = nullptr;   // around the per-march set-up
     cudaStream_t capture = nullptr;   // private stream for graph capture
     int64_t last_kernel_ns = 0;
+    int64_t last_setup_ns = 0;
     int64_t total_launches = 0;
 
     // layout (fixed once the medium is set)
@@ -51,12 +58,15 @@ struct pe3d_plan_s {
     std::vector<double> slice_r;
     void* mz = nullptr;               // [nslices][Nt][ldz]
     size_t mz_bytes = 0;
+    void* mzs = nullptr;              // [steps][Nt][ldz] per-step multipliers (interpolated medium)
+    size_t mzs_bytes = 0;
     // per-step arrays
     void* mB = nullptr;               // [steps][NtP]
     void* zsm = nullptr;              // [steps][NtP]
     void* gscr = nullptr;             // complex128 [2][steps][NtP] (periodic setup)
     void* sc = nullptr;               // StepConst [steps]
     int* slice_of_step = nullptr;     // [steps]
+    void* lerp = nullptr;             // MediumStep [steps] (interpolated medium)
     int step_cap = 0;
     void* rc_up = nullptr;            // FP64 residual correction buffers [Nt][ldz]
     void* rc_ut = nullptr;
@@ -121,6 +131,7 @@ int dev_alloc(pe3d_plan_s* p, void** ptr, size_t bytes);
 void dev_free(pe3d_plan_s* p, void** ptr, size_t bytes);
 int ensure_steps(pe3d_plan_s* p, int steps);
 int active_slice(const std::vector<double>& slice_r, double r);
+pe3d::MediumStep medium_step(const std::vector<double>& slice_r, double r);   // interpolation at r
 int encode_tmaps(pe3d_plan_s* p);   // tmap_v from v and the layout
 
 }  // namespace pe3d_host

@@ -96,6 +96,7 @@ struct MarchArgs {
     // FP64 residual correction every rc_every steps (0: off)
     int rc_every = 0;
     const double2* n2 = nullptr;  // complex128 [slices][Nt][Nz] (natural layout)
+    const MediumStep* lerp = nullptr;  // [steps]: n^2 interpolated in range (else nullptr)
     C* up = nullptr;              // u^j before a corrected step      [Nt][ldz]
     C* ut = nullptr;              // uncorrected u^{j+1}               [Nt][ldz]
     C* db = nullptr;              // correction d                      [Nt][ldz]
@@ -670,7 +671,10 @@ __device__ void residual_phase(const MarchArgs<C>& P, int j) {
     const double2 myq = make_double2(0.0, -kd * c / 4.0);
     const double2 alpha = make_double2(0.25, -kd / 4.0);
     const double2 beta = make_double2(0.25, kd / 4.0);
-    const double2* n2 = P.n2 + (size_t)P.slice_of_step[j] * P.Nt * P.Nz;
+    const size_t sl = (size_t)P.Nt * P.Nz;
+    const double2* n2 = P.n2 + (P.lerp ? (size_t)P.lerp[j].k : (size_t)P.slice_of_step[j]) * sl;
+    const double2* n2b = P.lerp ? P.n2 + (size_t)P.lerp[j].k1 * sl : n2;
+    const double tl = P.lerp ? P.lerp[j].t : 0.0;
     const long long n = (long long)P.Nt * P.ldz;
     for (long long idx = (long long)blockIdx.x * NT + threadIdx.x; idx < n; idx += (long long)gridDim.x * NT) {
         const int m = (int)(idx / P.ldz), l = (int)(idx - (long long)m * P.ldz);
@@ -689,6 +693,7 @@ __device__ void residual_phase(const MarchArgs<C>& P, int j) {
                 }
             }
             double2 q = n2[(size_t)m * P.Nz + l];
+            if (P.lerp) q = medium_lerp(q, n2b[(size_t)m * P.Nz + l], tl);
             q.x -= 1.0;
             const double2 x1 = cadd(cmul(q, t1[1]),
                                     make_double2(s * (t1[2].x + t1[0].x - 2.0 * t1[1].x),
@@ -957,34 +962,87 @@ __global__ void k_prologue(const C* __restrict__ u0, int Nz, int Nt, int ldz, in
 // FP64 coefficient setup ("update matrix A and B", Fig. 2 line 7)
 // ---------------------------------------------------------------------------
 
-// Depth systems of every slice: thread per (slice, azimuth).  Row l of
-// A = I + alpha X has diagonal d_l = 1 + alpha (n^2 - 1 - 2 s) and constant
-// off-diagonal e = alpha s; with pivots p_l = d_l - e^2 / p_{l-1} the stored
-// multiplier is mu_l = -e / p_l = -1 / (d_l / e + mu_{l-1}).
+// 1/x for 2^-53 <= x < 2^996: the hardware estimate (rcp.approx.ftz.f64)
+// refined by two Newton-Raphson steps y <- y + y (1 - x y), each of which
+// squares the relative error, so the result is within a few ulp of 1/x.  It
+// keeps the FP64 pipe (1/64 of the FP32 rate on this GPU) to one MUFU and four
+// FMAs per reciprocal.
+__device__ __forceinline__ double recip_newton(double x) {
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
+}
+
+// |den|^2 in [2^-53, 2^996): |mu| between about 1e-150 and 1e8.  Tested on the
+// exponent bits with integer operations (NaN, inf and 0 fall outside).
+__device__ __forceinline__ bool pivot_ok(double nrm) {
+    const unsigned hi = (unsigned)__double2hiint(nrm);
+    constexpr unsigned lo = (1023u - 53u) << 20, top = (1023u + 996u) << 20;
+    return hi - lo < top - lo;
+}
+
+// Depth systems: row l of A = I + alpha X has diagonal
+// d_l = 1 + alpha (n^2_l - 1 - 2 s) and constant off-diagonal e = alpha s; with
+// pivots p_l = d_l - e^2 / p_{l-1} the stored multiplier is
+// mu_l = -e / p_l = -1 / (d_l / e + mu_{l-1}).  d_l / e is written
+// ae n^2_l + ce with ae = alpha / e and ce = (1 - alpha (1 + 2 s)) / e, so a
+// depth point costs one complex FMA, the reciprocal and two products on the
+// FP64 pipe.  q_at(l) gives n^2_l.  Returns false if a pivot left the range
+// pivot_ok admits.
+template <typename C, typename Q>
+__device__ __forceinline__ bool depth_pivots(Q q_at, int Nz, int ldz, double2 alpha, double s, double2 einv,
+                                             C* __restrict__ out) {
+    const double2 ae = cmul(alpha, einv);
+    const double2 ce = csub(einv, cmul(ae, make_double2(1.0 + 2.0 * s, 0.0)));
+    double2 mprev = make_double2(0.0, 0.0);
+    bool ok = true;
+    for (int l = 0; l < Nz; ++l) {
+        const double2 q = q_at(l);
+        const double bx = ce.x + mprev.x, by = ce.y + mprev.y;
+        const double2 den = make_double2(fma(ae.x, q.x, fma(-ae.y, q.y, bx)),
+                                         fma(ae.x, q.y, fma(ae.y, q.x, by)));
+        const double nrm = fma(den.x, den.x, den.y * den.y);
+        ok &= pivot_ok(nrm);
+        const double inv = recip_newton(nrm);
+        const double2 mu = make_double2(-den.x * inv, den.y * inv);
+        out[l] = from64<C>(mu);
+        mprev = mu;
+    }
+    for (int l = Nz; l < ldz; ++l) out[l] = from64<C>(make_double2(0.0, 0.0));
+    return ok;
+}
+
+// Depth systems of every slice: thread per (slice, azimuth).
 template <typename C>
 __global__ void k_setupA(const double2* __restrict__ n2, int KNt, int Nz, int ldz, double2 alpha,
                          double s, double2 einv, C* __restrict__ mz, int* status) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= KNt) return;
     const double2* row = n2 + (size_t)idx * Nz;
-    C* out = mz + (size_t)idx * ldz;
-    double2 mprev = make_double2(0.0, 0.0);
-    bool bad = false;
-    for (int l = 0; l < Nz; ++l) {
-        double2 q = row[l];
-        q.x -= 1.0 + 2.0 * s;
-        double2 d = cmul(alpha, q);
-        d.x += 1.0;
-        const double2 den = cadd(cmul(d, einv), mprev);
-        const double nrm = den.x * den.x + den.y * den.y;
-        if (!(nrm >= 1e-16) || !(nrm < 1e300)) bad = true;
-        const double inv = 1.0 / nrm;
-        const double2 mu = make_double2(-den.x * inv, den.y * inv);
-        out[l] = from64<C>(mu);
-        mprev = mu;
-    }
-    for (int l = Nz; l < ldz; ++l) out[l] = from64<C>(make_double2(0.0, 0.0));
-    if (bad) atomicExch(status, ST_SINGULAR);
+    if (!depth_pivots<C>([row](int l) { return row[l]; }, Nz, ldz, alpha, s, einv, mz + (size_t)idx * ldz))
+        atomicExch(status, ST_SINGULAR);
+}
+
+// Depth systems of every range step when n^2 is interpolated in range
+// (thread per (step, azimuth)): the medium of step j is
+// (1 - t_j) n^2_k + t_j n^2_k1 from lerp[j], formed in FP64 as it is read.
+template <typename C>
+__global__ void k_setupA_lerp(const double2* __restrict__ n2, const MediumStep* __restrict__ lerp, int steps,
+                              int Nt, int Nz, int ldz, double2 alpha, double s, double2 einv,
+                              C* __restrict__ mz, int* status) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= steps * Nt) return;
+    const int j = idx / Nt, m = idx - j * Nt;
+    const MediumStep ms = lerp[j];
+    const double2* a = n2 + ((size_t)ms.k * Nt + m) * Nz;
+    const double2* b = n2 + ((size_t)ms.k1 * Nt + m) * Nz;
+    const double t = ms.t;
+    if (!depth_pivots<C>([a, b, t](int l) { return medium_lerp(a[l], b[l], t); }, Nz, ldz, alpha, s, einv,
+                         mz + (size_t)idx * ldz))
+        atomicExch(status, ST_SINGULAR);
 }
 
 // Azimuth systems of every step: thread per step j (and the Hankel factor of

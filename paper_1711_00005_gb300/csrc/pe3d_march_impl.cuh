@@ -119,7 +119,8 @@ void fill_args(pe3d_plan_s* p, MarchArgs<C>& A) {
     A.BY = p->BY; A.nload = p->nload; A.rowsB = p->rowsB;
     A.w = reinterpret_cast<C*>(p->w);
     A.v = reinterpret_cast<C*>(p->v);
-    A.mz = reinterpret_cast<const C*>(p->mz);
+    A.mz = reinterpret_cast<const C*>(p->interp ? p->mzs : p->mz);
+    A.lerp = p->interp ? reinterpret_cast<const MediumStep*>(p->lerp) : nullptr;
     A.slice_stride = (long long)p->Nt * p->ldz;
     A.slice_of_step = p->slice_of_step;
     A.mB = reinterpret_cast<const C*>(p->mB);
@@ -244,7 +245,37 @@ int step_setup(pe3d_plan_s* p, double r0, int steps, int stride) {
     int rc = ensure_steps(p, steps);
     if (rc) return rc;
     std::vector<int> sos(steps);
-    for (int j = 0; j < steps; ++j) sos[j] = active_slice(p->slice_r, r0 + (double)(j + 1) * p->dr);
+    if (p->interp) {
+        // n^2 at r* = r0 + (j+1) dr interpolated between the slices around it;
+        // the depth systems of every step are set up here, one row per step
+        std::vector<MediumStep> ms(steps);
+        for (int j = 0; j < steps; ++j) {
+            ms[j] = medium_step(p->slice_r, r0 + (double)(j + 1) * p->dr);
+            sos[j] = j;
+        }
+        const size_t mb = (size_t)steps * p->Nt * p->ldz * sizeof(C);
+        if (mb > p->mzs_bytes) {
+            dev_free(p, &p->mzs, p->mzs_bytes);
+            p->mzs_bytes = 0;
+            if ((rc = dev_alloc(p, &p->mzs, mb))) return rc;
+            p->mzs_bytes = mb;
+        }
+        PE3D_CUDA(cudaMemcpyAsync(p->lerp, ms.data(), sizeof(MediumStep) * steps, cudaMemcpyHostToDevice,
+                                  p->stream));
+        const double2 delta = d2(0.0, p->k0 * p->dr);
+        const double s = 1.0 / ((p->k0 * p->dz) * (p->k0 * p->dz));
+        const double2 alpha = d2(0.25 - delta.x / 4.0, -delta.y / 4.0);
+        const double2 einv = h_div(d2(1.0, 0.0), d2(alpha.x * s, alpha.y * s));
+        const long long n = (long long)steps * p->Nt;
+        if (n > INT_MAX) return fail(PE3D_ERR_ARG, "steps x Ntheta too large for an interpolated medium");
+        k_setupA_lerp<C><<<(int)((n + 127) / 128), 128, 0, p->stream>>>(
+            reinterpret_cast<const double2*>(p->n2), reinterpret_cast<const MediumStep*>(p->lerp), steps, p->Nt,
+            p->Nz, p->ldz, alpha, s, einv, reinterpret_cast<C*>(p->mzs), p->status);
+        PE3D_CUDA(cudaGetLastError());
+        p->total_launches += 1;
+    } else {
+        for (int j = 0; j < steps; ++j) sos[j] = active_slice(p->slice_r, r0 + (double)(j + 1) * p->dr);
+    }
     PE3D_CUDA(cudaMemcpyAsync(p->slice_of_step, sos.data(), sizeof(int) * steps, cudaMemcpyHostToDevice, p->stream));
     k_setupB<C><<<(steps + 127) / 128, 128, 0, p->stream>>>(
         steps, p->Nt, p->NtP, p->boundary == PE3D_PERIODIC, p->k0, p->dr, p->dtheta, r0,
@@ -329,8 +360,10 @@ int march(pe3d_plan_s* p, const void* u0_dev, double r0, int steps, int stride, 
     int rc = prepare_kernels<C>(p);
     if (rc) return rc;
     if (steps > 0) {
+        if (p->timing) PE3D_CUDA(cudaEventRecord(p->ev2, p->stream));
         rc = step_setup<C>(p, r0, steps, stride);
         if (rc) return rc;
+        if (p->timing) PE3D_CUDA(cudaEventRecord(p->ev3, p->stream));
     }
     rc = launch_prologue<C>(p, u0_dev, r0);
     if (rc) return rc;

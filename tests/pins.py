@@ -91,6 +91,31 @@ def check_dense(lib, periodic: bool, seed: int = 3, y_midpoint: bool = False) ->
     return err
 
 
+def check_interp_linear(lib, periodic: bool, y_midpoint: bool = False) -> float:
+    """Range-interpolated medium.  The slices sample n^2(r) = A + B (r - r0), so
+    the linear interpolation between them is that medium itself at every step
+    range inside their span, and the first (last) slice before (after) it.  The
+    interpolating march must equal dense Eq. 4 steps on those media; the steps
+    cover both sides of the span and two intervals inside it."""
+    wl = workloads.range_linear_case(6, 5, periodic=periodic, steps=9, seed=21)
+    g = wl.grid
+    A, B, R = wl.meta["A"], wl.meta["B"], wl.slice_r
+    got = lib.march(g, wl.n2, R, wl.u0, interp=True, y_midpoint=y_midpoint)
+    u = wl.u0.copy()
+    err = 0.0
+    for j in range(g.steps):
+        r = g.r0 + (j + 1) * g.dr
+        if r < R[0]:
+            n2j = wl.n2[0]
+        elif r >= R[-1]:
+            n2j = wl.n2[-1]
+        else:
+            n2j = A + B * (r - g.r0)
+        u = dense_step(u, n2j, g, y_range(g, j, y_midpoint))
+        err = max(err, relerr(got[j], u))
+    return err
+
+
 # --------------------------------------------------------------------------
 # closed-form discrete eigenmodes (homogeneous, theta-independent, real n0^2)
 # --------------------------------------------------------------------------
@@ -245,6 +270,10 @@ ALL_CHECKS = {
     "dense_periodic_mid": lambda L: check_dense(L, periodic=True, y_midpoint=True),
     "eig_walled_mid": lambda L: check_eigenmodes(L, False, 0.9, y_midpoint=True),
     "eig_periodic_mid": lambda L: check_eigenmodes(L, True, 0.9, y_midpoint=True),
+    # n^2 interpolated linearly in range
+    "interp_walled": lambda L: check_interp_linear(L, periodic=False),
+    "interp_periodic": lambda L: check_interp_linear(L, periodic=True),
+    "interp_walled_mid": lambda L: check_interp_linear(L, periodic=False, y_midpoint=True),
     "norm_walled": lambda L: check_norm_conservation(L, False),
     "norm_periodic": lambda L: check_norm_conservation(L, True),
     "reverse_walled": lambda L: check_reversibility(L, False),

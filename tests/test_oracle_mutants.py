@@ -34,6 +34,14 @@ MUTANTS = {
                                 "cplx lo = (m > 0) ? c : 0.0;"),
     # range bookkeeping
     "rstar_at_rj": ("double rstar = r0 + (double)(j + 1) * dr;", "double rstar = r0 + (double)j * dr;"),
+    # range interpolation of the medium
+    "interp_t_reversed": ("double t = (r - slice_r[k]) / (slice_r[k + 1] - slice_r[k]);",
+                          "double t = (slice_r[k + 1] - r) / (slice_r[k + 1] - slice_r[k]);"),
+    "interp_weights_swapped": ("out[i] = (1.0 - t) * a[i] + t * b[i];",
+                               "out[i] = t * a[i] + (1.0 - t) * b[i];"),
+    "interp_same_slice": ("*b = n2 + (size_t)(k + 1) * npts;", "*b = n2 + (size_t)k * npts;"),
+    "interp_ignored": ("        if (interp) {", "        if (0) {"),
+    "interp_hold_first": ("if (k + 1 >= K || r < slice_r[k]) {", "if (k + 1 >= K) {"),
     # solvers
     "backsub_index": ("- u2[i] * b[i + 2]) / d[i];", "- u2[i] * b[i + 1]) / d[i];"),
     "swap_fill_sign": ("if (i + 2 < n) u1[i + 1] = 0.0 - mult * r_i2;",

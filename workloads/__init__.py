@@ -374,3 +374,26 @@ def random_case(Nz: int, Ntheta: int, *, periodic: bool, K: int = 1, steps: int 
     R = r0 + (span / K) * np.arange(K)
     u0 = rng.normal(size=(Ntheta, Nz)) + 1j * rng.normal(size=(Ntheta, Nz))
     return Workload(g, R, np.ascontiguousarray(n2), u0.astype(np.complex128), {"seed": seed})
+
+
+def range_linear_case(Nz: int, Ntheta: int, *, periodic: bool, steps: int = 9, seed: int = 0,
+                      slice_steps=(2.5, 4.2, 6.0), k0: float = 0.4, dz: float = 2.0, dr: float = 5.0,
+                      r0: float = 100.0, dtheta: float | None = None, stride: int = 1) -> Workload:
+    """Slices that sample a medium linear in range, n^2(r) = A + B (r - r0),
+    at the non-uniform ranges r0 + slice_steps[k] dr.  A is rough and lossy
+    (real part in [0.85, 1.05], imaginary in [0.005, 0.02]), B moves n^2 by at
+    most 0.05 in real part and 0.004 in imaginary part over the slices' span.
+    meta holds A and B."""
+    rng = np.random.default_rng(seed)
+    if dtheta is None:
+        dtheta = (2 * math.pi / Ntheta) if periodic else math.radians(20.0) / (Ntheta + 1)
+    g = Grid(Nz=Nz, Ntheta=Ntheta, dz=dz, dtheta=dtheta, dr=dr, k0=k0, r0=r0,
+             steps=steps, stride=stride, periodic=periodic, theta_lo=-0.1, name="range-linear")
+    shape = (Ntheta, Nz)
+    A = rng.uniform(0.85, 1.05, size=shape) + 1j * rng.uniform(0.005, 0.02, size=shape)
+    span = max(slice_steps[-1] * dr, 1.0)
+    B = (rng.uniform(-0.05, 0.05, size=shape) + 1j * rng.uniform(-0.004, 0.004, size=shape)) / span
+    R = r0 + dr * np.asarray(slice_steps, dtype=np.float64)
+    n2 = np.stack([A + B * (r - r0) for r in R]).astype(np.complex128)
+    u0 = rng.normal(size=shape) + 1j * rng.normal(size=shape)
+    return Workload(g, R, np.ascontiguousarray(n2), u0.astype(np.complex128), {"seed": seed, "A": A, "B": B})
