@@ -103,10 +103,14 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+# the files the range-march kernels are built from
+MARCH_SOURCES = ("pe3d_device.cuh", "pe3d_f32.cu", "pe3d_f64.cu", "pe3d_kernels.cuh", "pe3d_march_impl.cuh")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1711_00005_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in MARCH_SOURCES:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
@@ -464,7 +468,7 @@ def run_ours(args):
         sns = statistics.mean(setup_ns) if setup_ns and setup_ns[0] > 0 else None
         if sns:
             line["setup"] = {"ms": sns / 1e6,
-                             "kernels": ("k_setupA_lerp + k_setupB" if interp else "k_setupB"),
+                             "kernels": "k_setupA_lerp + k_setupB" if interp else "k_setupB",
                              "note": "per-march set-up inside pe3d_march, CUDA events on the plan's stream"}
             if interp:
                 fl = SETUP_FLOPS_PER_POINT_STEP * point_steps

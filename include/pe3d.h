@@ -82,11 +82,15 @@ extern "C" {
                                    r0 + (j + 1/2) dr, the centred variant            */
 #define PE3D_OPT_MEDIUM_INTERP 9 /* 0: n^2 piecewise constant in range, slice k for
                                    R_k <= r* < R_{k+1} (default); 1: n^2 interpolated
-                                   linearly in range between the slices around r*,
-                                   with the depth systems set up in FP64 for every
-                                   range step of each march (Fig. 2 line 7 run per
-                                   step).  Costs Nt*ldz complex of the plan
-                                   precision per step of the longest march. */
+                                   linearly in range between the slices around r*
+                                   (held at the first/last slice outside their
+                                   span), with the depth systems set up in FP64 for
+                                   every range step of a march before it runs
+                                   (Fig. 2 line 7 run per step): Nt*ldz complex of
+                                   the plan precision per step of the longest
+                                   march.  pe3d_set_medium then keeps d/e of each
+                                   slice and its slope (32 B per grid point per
+                                   slice). */
 
 /* stored quantity (pe3d_set_option PE3D_OPT_OUTPUT), Fig. 2 lines 10 and 13 */
 #define PE3D_OUT_FIELD     0    /* the envelope u (default)                          */
@@ -205,6 +209,28 @@ int pe3d_march_batched(int n, const pe3d_plan_t *plans, const void *const *u0, c
 int pe3d_march_static(int Nz, int Ntheta, double dz, double dtheta, double dr, double k0, int boundary,
                       int precision, const void *n2, const double *slice_r, int K, const void *u0, double r0,
                       int steps, int out_stride, void *out, void *cuda_stream);
+
+/* Broadband synthesis: the time series at R receivers from the pressures of
+ * F single-frequency runs (a wide-band source is marched once per frequency,
+ * Fig. 1; Sec. 4 runs 8 and 120 frequencies).  The paper does not write the
+ * synthesis out; this library takes, with the e^{-i w t} convention under
+ * which H0^(1)(k0 r) is outgoing,
+ *   out[r][k] = Re sum_i W[i] p[i][r] exp(-2 pi i freqs[i] (t0 + k dt)),
+ * W[i] the source spectrum times the frequency-quadrature weight.
+ *   precision  PE3D_FP32 or PE3D_FP64: p and out in that precision
+ *   freqs      host double [F] (Hz), finite
+ *   W          host complex128 [F]
+ *   p          host array of F device pointers, each to R complex values
+ *              (e.g. a pressure snapshot of pe3d_march_batched, [Ntheta][Nz])
+ *   out        device real [R][T]
+ * The phases are formed in FP64 from f t reduced to a fraction of a cycle;
+ * the sum runs in the given precision.  Work and a stream-ordered scratch
+ * block of F*(32 + T*complex) bytes are enqueued on cuda_stream (NULL: the
+ * legacy default stream); the call returns once they are enqueued.  Errors:
+ * PE3D_ERR_ARG (bad sizes, non-finite inputs, p[i] or out not device
+ * memory), PE3D_ERR_OOM, PE3D_ERR_CUDA. */
+int pe3d_synthesize(int precision, int F, const double *freqs, const void *W, const void *const *p,
+                    long long R, int T, double t0, double dt, void *out, void *cuda_stream);
 
 /* Message for the calling thread's most recent failed call ("" if none). */
 const char *pe3d_last_error(void);

@@ -10,8 +10,11 @@ and cyclic solvers are pinned to LAPACK via numpy.linalg.solve and to the
 circulant FFT solution; the step is pinned to a dense LU solve of the printed
 Eq. 4 on tiny grids, to the closed-form discrete eigenmode multipliers, to
 exact norm conservation, to reversibility, to the theta-uniform reduction and
-to mirror symmetry (tests/test_oracle_pins.py); the pressure/TL output to
-Hankel's expansion and tabulated Bessel zeros (tests/test_oracle_output.py).
+to mirror symmetry (tests/test_oracle_pins.py); the interpolated medium to a
+medium linear in range (tests/pins.py); the pressure/TL output to Hankel's
+expansion and tabulated Bessel zeros (tests/test_oracle_output.py); the
+broadband synthesis to a single-frequency closed form, the FFT on a uniform
+frequency grid and the delay theorem (tests/test_oracle_synthesis.py).
 No value printed in the
 paper pins it: the paper prints no field values (parity to the paper's own
 outputs is unpinned).
@@ -162,3 +165,26 @@ def pressure(u_snaps, ranges, k0):
 def transmission_loss(p):
     """TL = -20 log10 |p| in dB (Fig. 2 line 13, Fig. 5)."""
     return -20.0 * np.log10(np.abs(p))
+
+
+# ---------------------------------------------------------------------------
+# broadband synthesis.  The paper runs the march once per frequency of a
+# wide-band signal (Fig. 1, the loop over frequencies; the 8- and
+# 120-frequency tests of Sec. 4) but does not write out how the time signal is
+# formed.  Reading taken: with the e^{-i w t} convention under which
+# H0^(1)(k0 r) is outgoing, a receiver's time series is the sum over the
+# computed frequencies s(t) = Re sum_i W_i p_i e^{-2 pi i f_i t}, W_i being the
+# source spectrum times the frequency-quadrature weight.
+# ---------------------------------------------------------------------------
+
+def synthesize(freqs, W, p, t0, dt, T):
+    """s[r][k] = Re sum_i W[i] p[i][r] exp(-2 pi i freqs[i] (t0 + k dt)) for
+    p of shape [F][R]: one frequency at a time, in FP64."""
+    freqs = np.asarray(freqs, dtype=np.float64)
+    W = np.asarray(W, dtype=np.complex128)
+    p = np.asarray(p, dtype=np.complex128).reshape(len(freqs), -1)
+    t = t0 + dt * np.arange(T, dtype=np.float64)
+    s = np.zeros((p.shape[1], T), np.float64)
+    for i in range(len(freqs)):
+        s += (W[i] * p[i][:, None] * np.exp(-2j * np.pi * freqs[i] * t[None, :])).real
+    return s

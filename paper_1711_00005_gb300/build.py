@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpe3d.so")
 SOURCES = ["pe3d_api.cu", "pe3d_f32.cu", "pe3d_f64.cu", "pe3d_server.cu", "pe3d_static.cu",
-           "pe3d_batch_f32.cu", "pe3d_batch_f64.cu"]
+           "pe3d_batch_f32.cu", "pe3d_batch_f64.cu", "pe3d_synth.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
               "-Xptxas", "-v", "-I", os.path.join(HERE, "..", "include")]

@@ -194,9 +194,9 @@ int pe3d_plan(int Nz, int Ntheta, double dz, double dtheta, double dr, double k0
 }
 
 // FP64 depth multipliers of every slice (Fig. 2 line 7).  An interpolated
-// medium sets its systems up per range step in the march instead.
+// medium gets each slice's d/e and its slope instead, and its systems are set
+// up per range step in the march.
 static int slice_setup(pe3d_plan_s* p) {
-    if (p->interp) return PE3D_OK;
     PE3D_CUDA(cudaMemsetAsync(p->status, 0, sizeof(int), p->stream));
     int rc = p->precision == PE3D_FP32 ? setupA_f32(p) : setupA_f64(p);
     if (rc) return rc;
@@ -248,8 +248,8 @@ int pe3d_set_option(pe3d_plan_t p, int option, int value) {
             if (value != 0 && value != 1) return fail(PE3D_ERR_ARG, "MEDIUM_INTERP must be 0 or 1");
             const int was = p->interp;
             p->interp = value;
-            // the per-slice multipliers are skipped while interpolating: build them on the way back
-            if (was && !value && p->medium_ready) return slice_setup(p);
+            // per-slice multipliers, or slopes for interpolation, of the medium already set
+            if (was != value && p->medium_ready) return slice_setup(p);
             return PE3D_OK;
         }
         case PE3D_OPT_RC_EVERY:
@@ -411,7 +411,7 @@ int pe3d_destroy(pe3d_plan_t p) {
     if (p->ev3) cudaEventDestroy(p->ev3);
     if (p->capture) cudaStreamDestroy(p->capture);
     void** bufs[] = {&p->w, &p->v, &p->u0stage, &p->outstage, &p->n2, &p->mz, &p->mB, &p->zsm, &p->batchbuf, &p->rc_up, &p->rc_ut, &p->rc_db,
-                     &p->gscr, &p->sc, (void**)&p->slice_of_step, &p->lerp, &p->mzs, (void**)&p->status, (void**)&p->bar};
+                     &p->gscr, &p->sc, (void**)&p->slice_of_step, &p->lerp, &p->mzs, &p->dd, (void**)&p->status, (void**)&p->bar};
     for (void** b : bufs)
         if (*b) { cudaFree(*b); *b = nullptr; }
     delete p;

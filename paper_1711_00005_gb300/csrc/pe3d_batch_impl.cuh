@@ -116,10 +116,11 @@ int batched_impl(int n, pe3d_plan_s* const* plans, const void* const* u0, const 
     if (rc) return rc;
     for (int i = 0; i < n; ++i) PE3D_CUDA(cudaMemsetAsync(plans[i]->status, 0, sizeof(int), owner->stream));
     std::vector<MarchArgs<C>> descs(n);
-    int nsteps = 0;
+    int nsteps = 0, ninterp = 0;
     for (int i = 0; i < n; ++i) {
         pe3d_plan_s* p = plans[i];
         if (steps[i] > 0 && (rc = step_setup<C>(p, r0[i], steps[i], stride[i]))) return rc;
+        ninterp += p->interp && steps[i] > 0;     // its per-step depth set-up
         if ((rc = launch_prologue<C>(p, u0[i], r0[i]))) return rc;
         fill_args<C>(p, descs[i]);
         descs[i].snap = reinterpret_cast<C*>(out[i]);
@@ -137,7 +138,7 @@ int batched_impl(int n, pe3d_plan_s* const* plans, const void* const* u0, const 
                            owner->status);
     if (rc) return rc;
     if (owner->timing) PE3D_CUDA(cudaEventRecord(owner->ev1, owner->stream));
-    owner->last_launches = 1 + 2 * n;
+    owner->last_launches = 1 + 2 * n + ninterp;
     owner->total_launches += owner->last_launches + n;
     return PE3D_OK;
 }

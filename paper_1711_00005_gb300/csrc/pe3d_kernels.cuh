@@ -987,23 +987,16 @@ __device__ __forceinline__ bool pivot_ok(double nrm) {
 // Depth systems: row l of A = I + alpha X has diagonal
 // d_l = 1 + alpha (n^2_l - 1 - 2 s) and constant off-diagonal e = alpha s; with
 // pivots p_l = d_l - e^2 / p_{l-1} the stored multiplier is
-// mu_l = -e / p_l = -1 / (d_l / e + mu_{l-1}).  d_l / e is written
-// ae n^2_l + ce with ae = alpha / e and ce = (1 - alpha (1 + 2 s)) / e, so a
-// depth point costs one complex FMA, the reciprocal and two products on the
-// FP64 pipe.  q_at(l) gives n^2_l.  Returns false if a pivot left the range
-// pivot_ok admits.
-template <typename C, typename Q>
-__device__ __forceinline__ bool depth_pivots(Q q_at, int Nz, int ldz, double2 alpha, double s, double2 einv,
-                                             C* __restrict__ out) {
-    const double2 ae = cmul(alpha, einv);
-    const double2 ce = csub(einv, cmul(ae, make_double2(1.0 + 2.0 * s, 0.0)));
+// mu_l = -e / p_l = -1 / (d_l / e + mu_{l-1}).  b_at(l) gives d_l / e; a depth
+// point then costs two adds, the reciprocal and two products on the FP64 pipe.
+// Returns false if a pivot left the range pivot_ok admits.
+template <typename C, typename B>
+__device__ __forceinline__ bool depth_pivots(B b_at, int Nz, int ldz, C* __restrict__ out) {
     double2 mprev = make_double2(0.0, 0.0);
     bool ok = true;
     for (int l = 0; l < Nz; ++l) {
-        const double2 q = q_at(l);
-        const double bx = ce.x + mprev.x, by = ce.y + mprev.y;
-        const double2 den = make_double2(fma(ae.x, q.x, fma(-ae.y, q.y, bx)),
-                                         fma(ae.x, q.y, fma(ae.y, q.x, by)));
+        const double2 b = b_at(l);
+        const double2 den = make_double2(b.x + mprev.x, b.y + mprev.y);
         const double nrm = fma(den.x, den.x, den.y * den.y);
         ok &= pivot_ok(nrm);
         const double inv = recip_newton(nrm);
@@ -1015,6 +1008,17 @@ __device__ __forceinline__ bool depth_pivots(Q q_at, int Nz, int ldz, double2 al
     return ok;
 }
 
+// d / e = ae n^2 + ce with ae = alpha / e and ce = (1 - alpha (1 + 2 s)) / e:
+// one complex FMA per point
+struct DiagOverE {
+    double2 ae, ce;
+    __device__ DiagOverE(double2 alpha, double s, double2 einv)
+        : ae(cmul(alpha, einv)), ce(csub(einv, cmul(cmul(alpha, einv), make_double2(1.0 + 2.0 * s, 0.0)))) {}
+    __device__ __forceinline__ double2 operator()(double2 q) const {
+        return make_double2(fma(ae.x, q.x, fma(-ae.y, q.y, ce.x)), fma(ae.x, q.y, fma(ae.y, q.x, ce.y)));
+    }
+};
+
 // Depth systems of every slice: thread per (slice, azimuth).
 template <typename C>
 __global__ void k_setupA(const double2* __restrict__ n2, int KNt, int Nz, int ldz, double2 alpha,
@@ -1022,26 +1026,50 @@ __global__ void k_setupA(const double2* __restrict__ n2, int KNt, int Nz, int ld
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= KNt) return;
     const double2* row = n2 + (size_t)idx * Nz;
-    if (!depth_pivots<C>([row](int l) { return row[l]; }, Nz, ldz, alpha, s, einv, mz + (size_t)idx * ldz))
+    const DiagOverE doe(alpha, s, einv);
+    if (!depth_pivots<C>([row, doe](int l) { return doe(row[l]); }, Nz, ldz, mz + (size_t)idx * ldz))
         atomicExch(status, ST_SINGULAR);
 }
 
-// Depth systems of every range step when n^2 is interpolated in range
-// (thread per (step, azimuth)): the medium of step j is
-// (1 - t_j) n^2_k + t_j n^2_k1 from lerp[j], formed in FP64 as it is read.
+// An interpolated medium, thread per grid point of each slice:
+// dd = (D_k, D_{k+1} - D_k) with D_k = d / e of slice k (the change is zero for
+// the last slice).  d / e is affine in n^2, so at (1 - t) n^2_k + t n^2_{k+1} it
+// is D_k + t (D_{k+1} - D_k).
 template <typename C>
-__global__ void k_setupA_lerp(const double2* __restrict__ n2, const MediumStep* __restrict__ lerp, int steps,
-                              int Nt, int Nz, int ldz, double2 alpha, double s, double2 einv,
-                              C* __restrict__ mz, int* status) {
+__global__ void k_setupA_slopes(const double2* __restrict__ n2, int K, long long pts, double2 alpha, double s,
+                                double2 einv, double4* __restrict__ dd) {
+    const DiagOverE doe(alpha, s, einv);
+    const long long n = (long long)K * pts;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double2 d0 = doe(n2[i]);
+        double2 dd1 = make_double2(0.0, 0.0);
+        if (i + pts < n) {
+            const double2 d1 = doe(n2[i + pts]);
+            dd1 = make_double2(d1.x - d0.x, d1.y - d0.y);
+        }
+        dd[i] = make_double4(d0.x, d0.y, dd1.x, dd1.y);
+    }
+}
+
+// Depth systems of range steps j_first .. j_first + count - 1 of an
+// interpolated medium (thread per (step, azimuth)), from the slopes of
+// k_setupA_slopes and lerp[j] = (k, k1, t): d / e = D_k + t (D_k1 - D_k).
+// Step j's multipliers go to slot j % ring of mz.
+template <typename C>
+__global__ void k_setupA_lerp(const double4* __restrict__ dd, const MediumStep* __restrict__ lerp, int j_first,
+                              int count, int ring, int Nt, int Nz, int ldz, C* __restrict__ mz, int* status) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= steps * Nt) return;
-    const int j = idx / Nt, m = idx - j * Nt;
+    if (idx >= count * Nt) return;
+    const int jj = idx / Nt, m = idx - jj * Nt;
+    const int j = j_first + jj;
     const MediumStep ms = lerp[j];
-    const double2* a = n2 + ((size_t)ms.k * Nt + m) * Nz;
-    const double2* b = n2 + ((size_t)ms.k1 * Nt + m) * Nz;
+    const double4* row = dd + ((size_t)ms.k * Nt + m) * Nz;
     const double t = ms.t;
-    if (!depth_pivots<C>([a, b, t](int l) { return medium_lerp(a[l], b[l], t); }, Nz, ldz, alpha, s, einv,
-                         mz + (size_t)idx * ldz))
+    C* out = mz + ((size_t)(j % ring) * Nt + m) * ldz;
+    if (!depth_pivots<C>([row, t](int l) {
+            const double4 q = row[l];
+            return make_double2(fma(t, q.z, q.x), fma(t, q.w, q.y));
+        }, Nz, ldz, out))
         atomicExch(status, ST_SINGULAR);
 }
 

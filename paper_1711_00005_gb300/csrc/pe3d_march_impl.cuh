@@ -94,13 +94,46 @@ int layout_choose(pe3d_plan_s* p) {
     return PE3D_OK;
 }
 
+// FP64 constants of the depth systems: alpha = (1 - d)/4, s = 1/(k0 dz)^2, 1/e
+struct DepthConsts {
+    double2 alpha, einv;
+    double s;
+};
+inline DepthConsts depth_consts(const pe3d_plan_s* p) {
+    DepthConsts c;
+    const double2 delta = d2(0.0, p->k0 * p->dr);
+    c.s = 1.0 / ((p->k0 * p->dz) * (p->k0 * p->dz));
+    c.alpha = d2(0.25 - delta.x / 4.0, -delta.y / 4.0);
+    c.einv = h_div(d2(1.0, 0.0), d2(c.alpha.x * c.s, c.alpha.y * c.s));
+    return c;
+}
+
+// Depth systems of every slice, or, for an interpolated medium, each slice's
+// d/e and its change to the next slice (the per-step systems are then built
+// in the march)
 template <typename C>
 int setupA(pe3d_plan_s* p) {
-    const double2 delta = d2(0.0, p->k0 * p->dr);
-    const double s = 1.0 / ((p->k0 * p->dz) * (p->k0 * p->dz));
-    const double2 alpha = d2(0.25 - delta.x / 4.0, -delta.y / 4.0);
-    const double2 e = d2(alpha.x * s, alpha.y * s);
-    const double2 einv = h_div(d2(1.0, 0.0), e);
+    const DepthConsts dc = depth_consts(p);
+    const double2 alpha = dc.alpha, einv = dc.einv;
+    const double s = dc.s;
+    if (p->interp) {
+        const long long pts = (long long)p->Nt * p->Nz;
+        const size_t b = (size_t)p->nslices * pts * sizeof(double4);
+        if (b != p->dd_bytes) {
+            dev_free(p, &p->dd, p->dd_bytes);
+            p->dd_bytes = 0;
+            int rc = dev_alloc(p, &p->dd, b);
+            if (rc) return rc;
+            p->dd_bytes = b;
+        }
+        const long long n = (long long)p->nslices * pts;
+        const int grid = (int)std::min<long long>((n + 255) / 256, 16LL * p->num_sms);
+        k_setupA_slopes<C><<<grid, 256, 0, p->stream>>>(reinterpret_cast<const double2*>(p->n2), p->nslices, pts,
+                                                        alpha, s, einv, reinterpret_cast<double4*>(p->dd));
+        PE3D_CUDA(cudaGetLastError());
+        p->total_launches += 1;
+        return PE3D_OK;
+    }
     const int KNt = p->nslices * p->Nt;
     k_setupA<C><<<(KNt + 127) / 128, 128, 0, p->stream>>>(
         reinterpret_cast<const double2*>(p->n2), KNt, p->Nz, p->ldz, alpha, s, einv,
@@ -239,15 +272,30 @@ int prepare_kernels(const pe3d_plan_s* p) {
     return PE3D_OK;
 }
 
-// per-step setup (FP64 azimuth pivots and step constants) + the slice table
+// Depth systems of steps [j_first, j_first + count) of an interpolated medium
+// into slots j % ring, on `st`
+template <typename C>
+int interp_setup(pe3d_plan_s* p, int j_first, int count, int ring, cudaStream_t st) {
+    const long long n = (long long)count * p->Nt;
+    if (n <= 0) return PE3D_OK;
+    if (n > INT_MAX) return fail(PE3D_ERR_ARG, "steps x Ntheta too large for an interpolated medium");
+    k_setupA_lerp<C><<<(int)((n + 127) / 128), 128, 0, st>>>(
+        reinterpret_cast<const double4*>(p->dd), reinterpret_cast<const MediumStep*>(p->lerp), j_first, count,
+        ring, p->Nt, p->Nz, p->ldz, reinterpret_cast<C*>(p->mzs), p->status);
+    PE3D_CUDA(cudaGetLastError());
+    return PE3D_OK;
+}
+
+// per-step setup (FP64 azimuth pivots and step constants) + the slice table.
+// An interpolated medium's depth systems of every step are set up here too
+// (step j's in slot j).
 template <typename C>
 int step_setup(pe3d_plan_s* p, double r0, int steps, int stride) {
     int rc = ensure_steps(p, steps);
     if (rc) return rc;
     std::vector<int> sos(steps);
     if (p->interp) {
-        // n^2 at r* = r0 + (j+1) dr interpolated between the slices around it;
-        // the depth systems of every step are set up here, one row per step
+        // n^2 at r* = r0 + (j+1) dr interpolated between the slices around it
         std::vector<MediumStep> ms(steps);
         for (int j = 0; j < steps; ++j) {
             ms[j] = medium_step(p->slice_r, r0 + (double)(j + 1) * p->dr);
@@ -262,17 +310,7 @@ int step_setup(pe3d_plan_s* p, double r0, int steps, int stride) {
         }
         PE3D_CUDA(cudaMemcpyAsync(p->lerp, ms.data(), sizeof(MediumStep) * steps, cudaMemcpyHostToDevice,
                                   p->stream));
-        const double2 delta = d2(0.0, p->k0 * p->dr);
-        const double s = 1.0 / ((p->k0 * p->dz) * (p->k0 * p->dz));
-        const double2 alpha = d2(0.25 - delta.x / 4.0, -delta.y / 4.0);
-        const double2 einv = h_div(d2(1.0, 0.0), d2(alpha.x * s, alpha.y * s));
-        const long long n = (long long)steps * p->Nt;
-        if (n > INT_MAX) return fail(PE3D_ERR_ARG, "steps x Ntheta too large for an interpolated medium");
-        k_setupA_lerp<C><<<(int)((n + 127) / 128), 128, 0, p->stream>>>(
-            reinterpret_cast<const double2*>(p->n2), reinterpret_cast<const MediumStep*>(p->lerp), steps, p->Nt,
-            p->Nz, p->ldz, alpha, s, einv, reinterpret_cast<C*>(p->mzs), p->status);
-        PE3D_CUDA(cudaGetLastError());
-        p->total_launches += 1;
+        if ((rc = interp_setup<C>(p, 0, steps, steps, p->stream))) return rc;
     } else {
         for (int j = 0; j < steps; ++j) sos[j] = active_slice(p->slice_r, r0 + (double)(j + 1) * p->dr);
     }
@@ -312,12 +350,12 @@ int run_steps(pe3d_plan_s* p, MarchArgs<C>& A, int steps) {
         int grid = 0;
         int rc = persistent_grid<C>(p, &A.sp, &grid);
         if (rc) return rc;
+        p->last_grid = grid;
         PE3D_CUDA(cudaMemsetAsync(p->bar, 0, sizeof(unsigned), p->stream));
         A.j0 = 0; A.j1 = steps;
         void* args[] = {&A};
         PE3D_CUDA(cudaLaunchCooperativeKernel(kt.persist[ca][cb], dim3(grid), dim3(NT), args, A.sp.total,
                                               p->stream));
-        p->last_grid = grid;
         p->last_launches = 1;
         if (p->timing) PE3D_CUDA(cudaEventRecord(p->ev1, p->stream));
         return PE3D_OK;
@@ -394,7 +432,8 @@ int march(pe3d_plan_s* p, const void* u0_dev, double r0, int steps, int stride, 
     }
     rc = run_steps<C>(p, A, steps);
     if (rc) return rc;
-    p->last_launches += 1 + (steps > 0 ? 1 : 0);   // prologue, azimuth setup
+    // prologue, azimuth set-up, and the per-step depth set-up of an interpolated medium
+    p->last_launches += 1 + (steps > 0 ? 1 : 0) + (p->interp && steps > 0 ? 1 : 0);
     p->total_launches += p->last_launches;
     return PE3D_OK;
 }

@@ -123,3 +123,26 @@ def test_interp_full_grid(P, oracle_lib):
     ref = oracle_lib.march(g, wl.n2, wl.slice_r, wl.u0, steps=40, stride=20, interp=True)
     got, _ = gpu_march(P, wl, fp32=True, steps=40, stride=20, interp=True)
     assert relerrs(got, ref).max() < TOL32
+
+
+@pytest.mark.parametrize("fp32", [False, True], ids=["fp64", "fp32"])
+def test_interp_wide_long_march(P, oracle_lib, fp32):
+    """Ntheta = 1024 over 96 steps and six slices: the persistent launch equals
+    the stream launch bit for bit and matches the oracle; so does a march with
+    the FP64 correction.  One march is four launches: the per-step depth
+    set-up, the azimuth set-up, the prologue and the persistent march."""
+    steps = 96
+    wl = workloads.random_case(64, 1024, periodic=True, K=6, steps=steps, seed=153, stride=24)
+    ref = oracle_lib.march(wl.grid, wl.n2, wl.slice_r, wl.u0, interp=True)
+    per, info = gpu_march(P, wl, fp32=fp32, exec_mode=3, interp=True)
+    assert info["launches"] == 4
+    stream, _ = gpu_march(P, wl, fp32=fp32, exec_mode=1, interp=True)
+    assert np.array_equal(per, stream)
+    assert relerrs(per, ref).max() < (TOL32 if fp32 else TOL64)
+    if fp32:
+        with P.Plan.for_grid(wl.grid, fp32=True, interp=True) as plan:
+            P.pe3d_set_option(plan.h, P.PE3D_OPT_RC_EVERY, 1)
+            plan.set_medium(torch.from_numpy(wl.n2).cuda(), wl.slice_r)
+            got = plan.march(torch.from_numpy(wl.u0.astype(np.complex64)).cuda(), wl.grid.r0, steps,
+                             wl.grid.stride).cpu().numpy()
+        assert relerrs(got, ref).max() < 2e-6
