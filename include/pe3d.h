@@ -177,7 +177,8 @@ int pe3d_autotune(pe3d_plan_t plan, double r0, int steps);
  * allowed; same precision and stream) in shared launches, the paper's
  * frequency loop (Fig. 2 lines 1 and 12; Sec. 3.2.3) on one GPU.  Per plan i
  * the arguments mean what they mean in pe3d_march; all pointers are device
- * memory.  Every launch advances every unfinished plan by one step.
+ * memory.  One cooperative launch advances up to 64 plans; a larger n runs
+ * as consecutive launches of up to 64 on the plans' stream.
  * Errors as pe3d_march. */
 int pe3d_march_batched(int n, const pe3d_plan_t *plans, const void *const *u0, const double *r0,
                        const int *steps, const int *out_stride, void *const *out);

@@ -97,6 +97,9 @@ _SIGS = {
                            ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                            ctypes.c_int, ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                            ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "pe3d_synthesize": ([ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                         ctypes.POINTER(ctypes.c_void_p), ctypes.c_longlong, ctypes.c_int, ctypes.c_double,
+                         ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "pe3d_server_create": ([ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)],
                            ctypes.c_int),
     "pe3d_submit": ([ctypes.c_void_p, ctypes.POINTER(pe3d_request), ctypes.POINTER(ctypes.c_uint64)],
@@ -237,6 +240,27 @@ def pe3d_march_static(Nz: int, Ntheta: int, dz: float, dtheta: float, dr: float,
                                             ctypes.c_void_p(r.ctypes.data), len(r), pu, float(r0), int(steps),
                                             int(out_stride), po, _stream_handle(cuda_stream)))
     del kn, ku, ko
+
+
+def pe3d_synthesize(precision: int, freqs, W, ps: Sequence, T: int, t0: float, dt: float, out,
+                    cuda_stream=None) -> None:
+    """Broadband synthesis out[r][k] = Re sum_i W[i] ps[i][r] e^{-2 pi i freqs[i] (t0 + k dt)}:
+    ps are F device tensors of R complex values each, out a device real tensor
+    [R][T] (see include/pe3d.h)."""
+    f = np.ascontiguousarray(freqs, dtype=np.float64)
+    w = np.ascontiguousarray(W, dtype=np.complex128)
+    F = len(f)
+    if len(w) != F or len(ps) != F:
+        raise ValueError("freqs, W and ps must have one entry per frequency")
+    R = ps[0].numel()
+    if any(p.numel() != R or not p.is_contiguous() for p in ps):
+        raise ValueError("every pressure tensor must be contiguous with R values")
+    arr = (ctypes.c_void_p * F)(*[p.data_ptr() for p in ps])
+    po, _, ko = _ptr(out)
+    _check(load_library().pe3d_synthesize(int(precision), F, ctypes.c_void_p(f.ctypes.data),
+                                          ctypes.c_void_p(w.ctypes.data), arr, int(R), int(T), float(t0),
+                                          float(dt), po, _stream_handle(cuda_stream)))
+    del ko
 
 
 def pe3d_last_error() -> str:

@@ -134,11 +134,20 @@ int batched_impl(int n, pe3d_plan_s* const* plans, const void* const* u0, const 
     }
     if (nsteps == 0) return PE3D_OK;
     if (owner->timing) PE3D_CUDA(cudaEventRecord(owner->ev0, owner->stream));
-    rc = launch_batched<C>(owner, descs, nsteps, owner->stream, &owner->batchbuf, &owner->batchbuf_bytes,
-                           owner->status);
-    if (rc) return rc;
+    // up to BATCH_MAX marches per launch; more run as consecutive launches on
+    // the same stream (each reuses the descriptor buffer after the previous one)
+    int groups = 0;
+    for (int b = 0; b < n; b += BATCH_MAX, ++groups) {
+        std::vector<MarchArgs<C>> part(descs.begin() + b, descs.begin() + std::min(n, b + BATCH_MAX));
+        int ns = 0;
+        for (int i = b; i < std::min(n, b + BATCH_MAX); ++i) ns = std::max(ns, steps[i]);
+        if (ns == 0) continue;
+        rc = launch_batched<C>(owner, part, ns, owner->stream, &owner->batchbuf, &owner->batchbuf_bytes,
+                               owner->status);
+        if (rc) return rc;
+    }
     if (owner->timing) PE3D_CUDA(cudaEventRecord(owner->ev1, owner->stream));
-    owner->last_launches = 1 + 2 * n + ninterp;
+    owner->last_launches = groups + 2 * n + ninterp;
     owner->total_launches += owner->last_launches + n;
     return PE3D_OK;
 }

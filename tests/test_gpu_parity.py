@@ -366,3 +366,27 @@ def test_autotune_keeps_parity(P, oracle_lib, fp32):
         assert info["zthreads"] in (32, 64, 128, 256) and info["ttile"] in (2, 4, 8, 16, 32)
         out = plan.march(torch.from_numpy(wl.u0.astype(cdt)).cuda(), g.r0, g.steps, g.stride).cpu().numpy()
     assert relerrs(out, ref).max() < (TOL32 if fp32 else TOL64)
+
+
+def test_batch_of_more_than_64_marches(P):
+    """70 marches: two consecutive batched launches of up to 64, each march
+    bit-identical to the same march alone."""
+    rng = np.random.default_rng(170)
+    wls = [workloads.random_case(int(rng.integers(20, 41)), int(rng.integers(3, 10)), periodic=bool(i % 2), K=2,
+                                 steps=int(rng.integers(3, 6)), seed=300 + i, stride=1) for i in range(70)]
+    plans, u0s, outs = [], [], []
+    for wl in wls:
+        pl = P.Plan.for_grid(wl.grid, fp32=True)
+        pl.set_medium(torch.from_numpy(wl.n2).cuda(), wl.slice_r)
+        plans.append(pl)
+        u0s.append(torch.from_numpy(wl.u0).to(torch.complex64).cuda())
+        outs.append(torch.zeros((wl.grid.steps, wl.grid.Ntheta, wl.grid.Nz), dtype=torch.complex64, device="cuda"))
+    P.pe3d_march_batched([p.h for p in plans], u0s, [wl.grid.r0 for wl in wls], [wl.grid.steps for wl in wls],
+                         [1] * len(wls), outs)
+    torch.cuda.synchronize()
+    assert P.pe3d_plan_info(plans[0].h)["launches"] == 2 + 2 * len(wls)
+    for i in (0, 1, 63, 64, 69):
+        alone, _ = gpu_march(P, wls[i], fp32=True)
+        assert np.array_equal(outs[i].cpu().numpy(), alone)
+    for pl in plans:
+        pl.close()

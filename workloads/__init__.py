@@ -133,11 +133,16 @@ def slice_ranges(r0: float, steps: int, dr: float, spacing: float) -> np.ndarray
     return r0 + spacing * np.arange(K)
 
 
-def gaussian_starter(grid: Grid, zs: float = 100.0, hann: bool | None = None) -> np.ndarray:
+def gaussian_starter(grid: Grid, zs: float = 100.0, hann: bool | None = None, image: bool = False) -> np.ndarray:
     """Gaussian starter sqrt(k0) exp(-k0^2 (z - zs)^2 / 2), times a Hann taper
-    sin^2(pi (m+1) / (Ntheta+1)) across a walled sector (uniform for 360 deg)."""
+    sin^2(pi (m+1) / (Ntheta+1)) across a walled sector (uniform for 360 deg).
+    With image, the source's mirror image in the pressure-release surface is
+    subtracted, sqrt(k0) [exp(-k0^2 (z - zs)^2 / 2) - exp(-k0^2 (z + zs)^2 / 2)],
+    so the starter vanishes at z = 0 as the field does."""
     k0 = grid.k0
     gz = math.sqrt(k0) * np.exp(-(k0 * k0) * (grid.z - zs) ** 2 / 2.0)
+    if image:
+        gz = gz - math.sqrt(k0) * np.exp(-(k0 * k0) * (grid.z + zs) ** 2 / 2.0)
     if hann is None:
         hann = not grid.periodic
     if hann:
@@ -397,3 +402,61 @@ def range_linear_case(Nz: int, Ntheta: int, *, periodic: bool, steps: int = 9, s
     n2 = np.stack([A + B * (r - r0) for r in R]).astype(np.complex128)
     u0 = rng.normal(size=shape) + 1j * rng.normal(size=shape)
     return Workload(g, R, np.ascontiguousarray(n2), u0.astype(np.complex128), {"seed": seed, "A": A, "B": B})
+
+
+@dataclass
+class Broadband:
+    """A wide-band source marched once per frequency on one shared grid, and the
+    synthesis parameters of its time series at the last range."""
+    members: list            # Workload per frequency (same grid but k0)
+    freqs: np.ndarray        # [F] Hz
+    W: np.ndarray            # [F] complex: source spectrum times the frequency step
+    t0: float                # first sample time [s]
+    dt: float                # sample spacing [s]
+    T: int                   # samples
+
+
+def broadband(F: int = 120, f_lo: float = 40.0, f_hi: float = 60.0, *, Nz: int = 384, Ntheta: int = 128,
+              steps: int = 800, T: int = 1024, slice_spacing: float = 500.0) -> Broadband:
+    """The paper's wide-band runs (Sec. 4: 8 and 120 frequencies on one grid)
+    at a size one GPU steps through in a fraction of a second.
+
+    F frequencies uniform over [f_lo, f_hi]; one grid resolving f_hi
+    (dz = lambda/8 at f_hi, 3.125 m for 60 Hz; dr = lambda/4, 6.25 m; 30 deg
+    walled sector), r0 = 100 m, `steps` range steps (5 km at 800).  The medium
+    is the walled 100 Hz case's kind at depth Nz*dz: Munk profile with seed-3
+    perturbations (sigma 2 m/s, ell 50 m), a planar bottom D = 200 + 0.1 r
+    cos(theta) with 1700 m/s below it and an absorbing bottom 20 % of the grid,
+    one slice every `slice_spacing` m; it does not depend on frequency.  Each
+    member starts from the Gaussian starter at its own k0.  The source spectrum
+    is a Hann window over the band; W_i is it times the frequency step.  The
+    series has T samples at 200 Hz (above twice f_hi), starting 1 s before the
+    arrival time r_end / C0 at the last range."""
+    freqs = np.linspace(f_lo, f_hi, F) if F > 1 else np.array([0.5 * (f_lo + f_hi)])
+    lam = C0 / f_hi
+    dz, dr = lam / 8.0, lam / 4.0
+    sector = math.radians(30.0)
+    g0 = Grid(Nz=Nz, Ntheta=Ntheta, dz=dz, dtheta=sector / (Ntheta + 1), dr=dr, k0=0.0, r0=100.0,
+              steps=steps, stride=steps, periodic=False, theta_lo=-sector / 2, name="broadband")
+    pert = FourierPerturbation(seed=3, sigma=2.0, ell=50.0)
+    R = slice_ranges(g0.r0, steps, dr, slice_spacing)
+    z, th = g0.z, g0.theta
+    depth = Nz * dz
+    cz = munk(z)
+    im = _absorber(z, 0.8 * depth, depth)
+    n2 = np.empty((len(R), Ntheta, Nz), np.complex128)
+    for k, r in enumerate(R):
+        D = 200.0 + 0.1 * r * np.cos(th)
+        c = cz[None, :] + pert.slice(r, th, z)
+        c = np.where(z[None, :] > D[:, None], 1700.0, c)
+        n2[k] = _n2(c, np.broadcast_to(im, c.shape))
+    members = []
+    for f in freqs:
+        g = Grid(**{**g0.__dict__, "k0": 2 * math.pi * f / C0, "freq": float(f),
+                    "name": f"broadband-{F}f-{f_lo:g}-{f_hi:g}Hz-{Nz}x{Ntheta}-{steps}steps"})
+        members.append(Workload(g, R, n2, gaussian_starter(g), {"seed": 3}))
+    df = (f_hi - f_lo) / (F - 1) if F > 1 else 1.0
+    hann = np.sin(np.pi * (freqs - f_lo) / (f_hi - f_lo)) ** 2 if F > 1 else np.ones(1)
+    W = (hann * df).astype(np.complex128)
+    r_end = g0.r0 + steps * dr
+    return Broadband(members, freqs, W, r_end / C0 - 1.0, 1.0 / 200.0, T)
