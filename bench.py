@@ -519,8 +519,7 @@ def run_batched(args):
     torch.cuda.synchronize()
 
     def step():
-        for h, n2, wl in zip(plans, n2s, wls):
-            P.pe3d_set_medium(h, n2, wl.slice_r)
+        P.pe3d_set_medium_batched(plans, n2s, [wl.slice_r for wl in wls])
         P.pe3d_march_batched(plans, u0s, [g.r0 for g in grids], [g.steps for g in grids],
                              [g.stride for g in grids], outs)
 
@@ -564,8 +563,7 @@ def run_batched(args):
     u0h = [torch.from_numpy(wl.u0.astype(np.complex64)).pin_memory() for wl in wls]
     outh = [torch.empty((1, g.Ntheta, g.Nz), dtype=torch.complex64).pin_memory() for g in grids]
     t0 = time.perf_counter()
-    for h, n2, wl in zip(plans, n2h, wls):
-        P.pe3d_set_medium(h, n2, wl.slice_r)
+    P.pe3d_set_medium_batched(plans, n2h, [wl.slice_r for wl in wls])
     for u, ud in zip(u0h, u0s):
         ud.copy_(u, non_blocking=True)
     P.pe3d_march_batched(plans, u0s, [g.r0 for g in grids], [g.steps for g in grids],
@@ -591,8 +589,9 @@ def run_batched(args):
         "e2e": {"value": point_steps / t_e2e, "unit": UNIT,
                 "h2d_bytes_per_step": int(sum(wl.n2.nbytes for wl in wls) + sum(u.numel() * 8 for u in u0h)),
                 "d2h_bytes_per_step": int(sum(o.numel() * 8 for o in outh))},
-        # per step and march: depth setup, azimuth setup, prologue; plus the one batched march
-        "gpu_launches": int(len(plans) * 3 + 1) * args.steps,
+        # per step: one depth set-up and one azimuth set-up for all marches, a prologue per
+        # march, the batched march
+        "gpu_launches": int(2 + len(plans) + 1) * args.steps,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -639,8 +638,7 @@ def run_broadband(args):
     series = torch.empty((R, bb.T), dtype=torch.float32, device=dev)
     slice_r = bb.members[0].slice_r
     def step(timed_synthesis=None):
-        for h in plans:
-            P.pe3d_set_medium(h, n2, slice_r)
+        P.pe3d_set_medium_batched(plans, [n2] * F, [slice_r] * F)
         P.pe3d_march_batched(plans, u0s, [x.r0 for x in grids], [x.steps for x in grids],
                              [x.stride for x in grids], outs)
         if timed_synthesis is not None:
@@ -703,8 +701,7 @@ def run_broadband(args):
     sh = torch.empty((R, bb.T), dtype=torch.float32).pin_memory()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for h in plans:
-        P.pe3d_set_medium(h, n2h, slice_r)
+    P.pe3d_set_medium_batched(plans, [n2h] * F, [slice_r] * F)
     with torch.cuda.stream(stream):
         for u, ud in zip(u0h, u0s):
             ud.copy_(u, non_blocking=True)
@@ -723,7 +720,8 @@ def run_broadband(args):
                    "Nz": g.Nz, "Ntheta": g.Ntheta, "range_steps": g.steps, "point_steps_per_launch": point_steps,
                    "series": {"receivers": R, "samples": bb.T, "dt_s": bb.dt},
                    "precision": "complex64 march and synthesis, FP64 coefficients and phases",
-                   "exec": "per-frequency FP64 set-up, one batched persistent launch, pe3d_synthesize",
+                   "exec": "FP64 set-up of all frequencies in one launch each (depth, azimuth), batched "
+                           "persistent launches of up to 64 marches, pe3d_synthesize",
                    "l2": "working set (120 marches' fields and coefficients, ~1.5 GB) exceeds the 129 MB L2"},
         "max_rel_l2_vs_oracle": err,
         "synthesis_rel_l2_vs_oracle": err_syn,
@@ -739,9 +737,9 @@ def run_broadband(args):
         "e2e": {"value": point_steps / t_e2e, "unit": UNIT,
                 "h2d_bytes_per_step": int(F * bb.members[0].n2.nbytes + sum(u.numel() * 8 for u in u0h)),
                 "d2h_bytes_per_step": int(sh.numel() * 4)},
-        # per step: three set-up launches per frequency, the batched march (64 marches per
-        # launch), two synthesis kernels
-        "gpu_launches": int(F * 3 + -(-F // 64) + 2) * args.steps,
+        # per step: one depth and one azimuth set-up for all frequencies, a prologue per
+        # frequency, the batched march (64 marches per launch), two synthesis kernels
+        "gpu_launches": int(2 + F + -(-F // 64) + 2) * args.steps,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)

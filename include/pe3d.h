@@ -151,6 +151,16 @@ int pe3d_set_medium(pe3d_plan_t plan, const void *n2, const double *slice_r, int
 int pe3d_march(pe3d_plan_t plan, const void *u0, int u0_on_device, double r0, int steps,
                int out_stride, void *out, int out_on_device);
 
+/* pe3d_set_medium for n plans at once (same precision and stream; no plan
+ * twice): plan i gets n2[i], slice_r[i], K[i], all on the device or all on
+ * the host (n2_on_device).  The depth systems of every plan's slices are built
+ * in one launch, so many small set-ups (one per frequency of a wide-band run)
+ * share the FP64 pipe instead of each leaving it nearly idle; the stream is
+ * synchronised once.  Each plan ends as pe3d_set_medium would leave it.
+ * Errors as pe3d_set_medium; on an error no plan's medium is ready. */
+int pe3d_set_medium_batched(int n, const pe3d_plan_t *plans, const void *const *n2, const double *const *slice_r,
+                            const int *K, int n2_on_device);
+
 /* Release a plan and its device memory (synchronises its stream). */
 int pe3d_destroy(pe3d_plan_t plan);
 

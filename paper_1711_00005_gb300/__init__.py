@@ -97,6 +97,9 @@ _SIGS = {
                            ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                            ctypes.c_int, ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                            ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "pe3d_set_medium_batched": ([ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                 ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int), ctypes.c_int],
+                                ctypes.c_int),
     "pe3d_synthesize": ([ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                          ctypes.POINTER(ctypes.c_void_p), ctypes.c_longlong, ctypes.c_int, ctypes.c_double,
                          ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
@@ -240,6 +243,25 @@ def pe3d_march_static(Nz: int, Ntheta: int, dz: float, dtheta: float, dr: float,
                                             ctypes.c_void_p(r.ctypes.data), len(r), pu, float(r0), int(steps),
                                             int(out_stride), po, _stream_handle(cuda_stream)))
     del kn, ku, ko
+
+
+def pe3d_set_medium_batched(plans: Sequence, n2s: Sequence, slice_rs: Sequence) -> None:
+    """pe3d_set_medium for several plans in one depth set-up launch; n2s all
+    device tensors or all host arrays (see include/pe3d.h)."""
+    n = len(plans)
+    if len(n2s) != n or len(slice_rs) != n:
+        raise ValueError("one medium and one slice-range array per plan")
+    ptrs = [_ptr(x) for x in n2s]
+    on_dev = {d for _, d, _ in ptrs}
+    if len(on_dev) != 1:
+        raise ValueError("media must be all on the device or all on the host")
+    rs = [np.ascontiguousarray(r, dtype=np.float64) for r in slice_rs]
+    Pl = (ctypes.c_void_p * n)(*[p.value if isinstance(p, ctypes.c_void_p) else p for p in plans])
+    N2 = (ctypes.c_void_p * n)(*[p for p, _, _ in ptrs])
+    RS = (ctypes.c_void_p * n)(*[r.ctypes.data for r in rs])
+    KK = (ctypes.c_int * n)(*[len(r) for r in rs])
+    _check(load_library().pe3d_set_medium_batched(n, Pl, N2, RS, KK, on_dev.pop()))
+    del ptrs, rs
 
 
 def pe3d_synthesize(precision: int, freqs, W, ps: Sequence, T: int, t0: float, dt: float, out,

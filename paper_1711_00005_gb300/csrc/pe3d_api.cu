@@ -279,8 +279,8 @@ int pe3d_get_option(pe3d_plan_t p, int option, int* value) {
     }
 }
 
-int pe3d_set_medium(pe3d_plan_t p, const void* n2, const double* slice_r, int K, int n2_on_device) {
-    g_err.clear();
+// Check and upload one plan's medium (no coefficient set-up yet)
+static int upload_medium(pe3d_plan_s* p, const void* n2, const double* slice_r, int K, int n2_on_device) {
     if (!p || !n2 || !slice_r) return fail(PE3D_ERR_ARG, "NULL argument");
     if (K < 1) return fail(PE3D_ERR_ARG, "K must be >= 1");
     for (int k = 0; k < K; ++k) {
@@ -309,8 +309,51 @@ int pe3d_set_medium(pe3d_plan_t p, const void* n2, const double* slice_r, int K,
                               p->stream));
     p->nslices = K;
     p->slice_r.assign(slice_r, slice_r + K);
+    return PE3D_OK;
+}
+
+int pe3d_set_medium(pe3d_plan_t p, const void* n2, const double* slice_r, int K, int n2_on_device) {
+    g_err.clear();
+    int rc = upload_medium(p, n2, slice_r, K, n2_on_device);
+    if (rc) return rc;
     if ((rc = slice_setup(p))) return rc;
     p->medium_ready = true;
+    return PE3D_OK;
+}
+
+int pe3d_set_medium_batched(int n, const pe3d_plan_t* plans, const void* const* n2, const double* const* slice_r,
+                            const int* K, int n2_on_device) {
+    g_err.clear();
+    if (n < 1 || !plans || !n2 || !slice_r || !K) return fail(PE3D_ERR_ARG, "NULL argument");
+    for (int i = 0; i < n; ++i) {
+        if (!plans[i]) return fail(PE3D_ERR_ARG, "plan is NULL");
+        if (plans[i]->precision != plans[0]->precision) return fail(PE3D_ERR_ARG, "plans must share one precision");
+        if (plans[i]->stream != plans[0]->stream) return fail(PE3D_ERR_ARG, "plans must share one stream");
+        for (int k = 0; k < i; ++k)
+            if (plans[k] == plans[i]) return fail(PE3D_ERR_ARG, "a plan appears twice");
+    }
+    for (int i = 0; i < n; ++i) plans[i]->medium_ready = false;
+    int rc;
+    for (int i = 0; i < n; ++i)
+        if ((rc = upload_medium(plans[i], n2[i], slice_r[i], K[i], n2_on_device))) return rc;
+    // one depth set-up launch for the piecewise media; interpolated ones get their slopes
+    std::vector<pe3d_plan_s*> flat;
+    for (int i = 0; i < n; ++i) {
+        PE3D_CUDA(cudaMemsetAsync(plans[i]->status, 0, sizeof(int), plans[i]->stream));
+        if (plans[i]->interp) {
+            if ((rc = plans[i]->precision == PE3D_FP32 ? setupA_f32(plans[i]) : setupA_f64(plans[i]))) return rc;
+        } else {
+            flat.push_back(plans[i]);
+        }
+    }
+    if (!flat.empty()) {
+        rc = plans[0]->precision == PE3D_FP32 ? setupA_multi_f32(flat.data(), (int)flat.size())
+                                              : setupA_multi_f64(flat.data(), (int)flat.size());
+        if (rc) return rc;
+    }
+    for (int i = 0; i < n; ++i)
+        if ((rc = read_status(plans[i]))) return rc;
+    for (int i = 0; i < n; ++i) plans[i]->medium_ready = true;
     return PE3D_OK;
 }
 
@@ -411,7 +454,8 @@ int pe3d_destroy(pe3d_plan_t p) {
     if (p->ev3) cudaEventDestroy(p->ev3);
     if (p->capture) cudaStreamDestroy(p->capture);
     void** bufs[] = {&p->w, &p->v, &p->u0stage, &p->outstage, &p->n2, &p->mz, &p->mB, &p->zsm, &p->batchbuf, &p->rc_up, &p->rc_ut, &p->rc_db,
-                     &p->gscr, &p->sc, (void**)&p->slice_of_step, &p->lerp, &p->mzs, &p->dd, (void**)&p->status, (void**)&p->bar};
+                     &p->gscr, &p->sc, (void**)&p->slice_of_step, &p->lerp, &p->mzs, &p->dd, &p->setupbuf, (void**)&p->status,
+                     (void**)&p->bar};
     for (void** b : bufs)
         if (*b) { cudaFree(*b); *b = nullptr; }
     delete p;

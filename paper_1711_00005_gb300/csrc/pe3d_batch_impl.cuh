@@ -116,10 +116,17 @@ int batched_impl(int n, pe3d_plan_s* const* plans, const void* const* u0, const 
     if (rc) return rc;
     for (int i = 0; i < n; ++i) PE3D_CUDA(cudaMemsetAsync(plans[i]->status, 0, sizeof(int), owner->stream));
     std::vector<MarchArgs<C>> descs(n);
+    std::vector<SetupBArgs<C>> bargs;
+    std::vector<int> bsteps;
     int nsteps = 0, ninterp = 0;
     for (int i = 0; i < n; ++i) {
         pe3d_plan_s* p = plans[i];
-        if (steps[i] > 0 && (rc = step_setup<C>(p, r0[i], steps[i], stride[i]))) return rc;
+        if (steps[i] > 0) {
+            // tables here; the azimuth systems of all marches in one launch below
+            if ((rc = step_setup<C>(p, r0[i], steps[i], stride[i], false))) return rc;
+            bargs.push_back(setupB_args<C>(p, r0[i], steps[i], stride[i]));
+            bsteps.push_back(steps[i]);
+        }
         ninterp += p->interp && steps[i] > 0;     // its per-step depth set-up
         if ((rc = launch_prologue<C>(p, u0[i], r0[i]))) return rc;
         fill_args<C>(p, descs[i]);
@@ -133,6 +140,8 @@ int batched_impl(int n, pe3d_plan_s* const* plans, const void* const* u0, const 
         p->last_exec = PE3D_EXEC_PERSISTENT;
     }
     if (nsteps == 0) return PE3D_OK;
+    if ((rc = launch_multi<SetupBArgs<C>>(owner, bargs, bsteps, k_setupB_multi<C>))) return rc;
+    owner->total_launches -= 1;                   // counted below with this call's other launches
     if (owner->timing) PE3D_CUDA(cudaEventRecord(owner->ev0, owner->stream));
     // up to BATCH_MAX marches per launch; more run as consecutive launches on
     // the same stream (each reuses the descriptor buffer after the previous one)
@@ -147,8 +156,9 @@ int batched_impl(int n, pe3d_plan_s* const* plans, const void* const* u0, const 
         if (rc) return rc;
     }
     if (owner->timing) PE3D_CUDA(cudaEventRecord(owner->ev1, owner->stream));
-    owner->last_launches = groups + 2 * n + ninterp;
-    owner->total_launches += owner->last_launches + n;
+    // batched launches, one prologue per march, the azimuth set-up, interpolated depth set-ups
+    owner->last_launches = groups + n + 1 + ninterp;
+    owner->total_launches += owner->last_launches;
     return PE3D_OK;
 }
 

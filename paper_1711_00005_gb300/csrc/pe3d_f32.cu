@@ -4,6 +4,7 @@
 namespace pe3d_host {
 int layout_choose_f32(pe3d_plan_s* p) { return layout_choose<float2>(p); }
 int setupA_f32(pe3d_plan_s* p) { return setupA<float2>(p); }
+int setupA_multi_f32(pe3d_plan_s* const* plans, int n) { return setupA_multi<float2>(plans, n); }
 void persistent_config_f32(const pe3d_plan_s* p, SmemPlan* sp, int* grid) { persistent_config<float2>(p, sp, grid); }
 int march_f32(pe3d_plan_s* p, const void* u0, double r0, int steps, int stride, void* snap, int snap_ld) {
     return march<float2>(p, u0, r0, steps, stride, snap, snap_ld);

@@ -4,6 +4,7 @@
 namespace pe3d_host {
 int layout_choose_f64(pe3d_plan_s* p) { return layout_choose<double2>(p); }
 int setupA_f64(pe3d_plan_s* p) { return setupA<double2>(p); }
+int setupA_multi_f64(pe3d_plan_s* const* plans, int n) { return setupA_multi<double2>(plans, n); }
 void persistent_config_f64(const pe3d_plan_s* p, SmemPlan* sp, int* grid) { persistent_config<double2>(p, sp, grid); }
 int march_f64(pe3d_plan_s* p, const void* u0, double r0, int steps, int stride, void* snap, int snap_ld) {
     return march<double2>(p, u0, r0, steps, stride, snap, snap_ld);

@@ -75,6 +75,8 @@ struct pe3d_plan_s {
     void* rc_db = nullptr;
     void* batchbuf = nullptr;         // batch descriptors (when this plan leads a batch)
     size_t batchbuf_bytes = 0;
+    void* setupbuf = nullptr;         // multi-plan set-up descriptors (when this plan leads one)
+    size_t setupbuf_bytes = 0;
     int* status = nullptr;            // device status word
     unsigned* bar = nullptr;          // grid-barrier counter
     bool medium_ready = false;
@@ -103,6 +105,9 @@ size_t elem_bytes(const pe3d_plan_s* p);   // 8 (FP32) or 16 (FP64)
 int layout_choose_f32(pe3d_plan_s* p);
 int layout_choose_f64(pe3d_plan_s* p);
 int setupA_f32(pe3d_plan_s* p);
+// depth set-up of n plans (same precision and stream) in one launch, on plans[0]'s stream
+int setupA_multi_f32(pe3d_plan_s* const* plans, int n);
+int setupA_multi_f64(pe3d_plan_s* const* plans, int n);
 int setupA_f64(pe3d_plan_s* p);
 int march_f32(pe3d_plan_s* p, const void* u0_dev, double r0, int steps, int stride, void* snap_dev, int snap_ld);
 int march_f64(pe3d_plan_s* p, const void* u0_dev, double r0, int steps, int stride, void* snap_dev, int snap_ld);

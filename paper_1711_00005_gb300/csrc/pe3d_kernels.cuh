@@ -1019,16 +1019,59 @@ struct DiagOverE {
     }
 };
 
+// One depth system (one slice and azimuth): n^2 row -> multipliers.  Not
+// inlined, so the single-plan and the multi-plan kernels run the same code
+// and build bit-identical multipliers.
+template <typename C>
+__device__ __noinline__ void depth_system(const double2* __restrict__ row, int Nz, int ldz, double2 alpha,
+                                          double s, double2 einv, C* __restrict__ out, int* status) {
+    const DiagOverE doe(alpha, s, einv);
+    if (!depth_pivots<C>([row, doe](int l) { return doe(row[l]); }, Nz, ldz, out)) atomicExch(status, ST_SINGULAR);
+}
+
 // Depth systems of every slice: thread per (slice, azimuth).
 template <typename C>
 __global__ void k_setupA(const double2* __restrict__ n2, int KNt, int Nz, int ldz, double2 alpha,
                          double s, double2 einv, C* __restrict__ mz, int* status) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= KNt) return;
-    const double2* row = n2 + (size_t)idx * Nz;
-    const DiagOverE doe(alpha, s, einv);
-    if (!depth_pivots<C>([row, doe](int l) { return doe(row[l]); }, Nz, ldz, mz + (size_t)idx * ldz))
-        atomicExch(status, ST_SINGULAR);
+    depth_system<C>(n2 + (size_t)idx * Nz, Nz, ldz, alpha, s, einv, mz + (size_t)idx * ldz, status);
+}
+
+// Per-plan arguments of the multi-plan set-up kernels
+template <typename C>
+struct SetupADesc {
+    const double2* n2;
+    C* mz;
+    int* status;
+    int Nz, ldz;
+    double2 alpha, einv;
+    double s;
+};
+
+// index of the plan owning global work item idx: prefix[i] <= idx < prefix[i+1]
+__device__ __forceinline__ int owner_of(const int* __restrict__ prefix, int n, int idx) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (prefix[mid] <= idx) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Depth systems of every slice of n plans in one launch (thread per plan,
+// slice and azimuth; prefix[i] = systems of plans before i), so that many
+// small set-ups fill the FP64 pipe together instead of one latency-bound
+// launch each.
+template <typename C>
+__global__ void k_setupA_multi(const SetupADesc<C>* __restrict__ d, const int* __restrict__ prefix, int n) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= prefix[n]) return;
+    const int i = owner_of(prefix, n, idx);
+    const SetupADesc<C> a = d[i];
+    const int sys = idx - prefix[i];
+    depth_system<C>(a.n2 + (size_t)sys * a.Nz, a.Nz, a.ldz, a.alpha, a.s, a.einv, a.mz + (size_t)sys * a.ldz,
+                    a.status);
 }
 
 // An interpolated medium, thread per grid point of each slice:
@@ -1073,17 +1116,35 @@ __global__ void k_setupA_lerp(const double4* __restrict__ dd, const MediumStep* 
         atomicExch(status, ST_SINGULAR);
 }
 
-// Azimuth systems of every step: thread per step j (and the Hankel factor of
-// the pressure output on snapshot steps).  B_j = I - (d/4) Y_j has
-// diagonal 1 + d c_j / 2 and off-diagonal e_B = -d c_j / 4, the same for every
-// depth.  Full circle: T = B - u v^T with gamma = -diag, u = (gamma, 0.., e_B),
-// v = (1, 0.., e_B / gamma); z = T^-1 u and xi = 1 / (1 + v.z) are FP64.
+// Per-plan arguments of the azimuth set-up
 template <typename C>
-__global__ void k_setupB(int steps, int Nt, int NtP, int periodic, double k0, double dr, double dtheta,
-                         double r0, C* __restrict__ mB, C* __restrict__ zsm, double2* __restrict__ gscr,
-                         StepConst* __restrict__ sc, int* status, int hk_stride, int y_mid) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= steps) return;
+struct SetupBArgs {
+    int steps, Nt, NtP, periodic;
+    double k0, dr, dtheta, r0;
+    C* mB;
+    C* zsm;
+    double2* gscr;
+    StepConst* sc;
+    int* status;
+    int hk_stride, y_mid;
+};
+
+// Azimuth system of step j of one plan (and the Hankel factor of the pressure
+// output on snapshot steps).  B_j = I - (d/4) Y_j has diagonal 1 + d c_j / 2
+// and off-diagonal e_B = -d c_j / 4, the same for every depth.  Full circle:
+// T = B - u v^T with gamma = -diag, u = (gamma, 0.., e_B),
+// v = (1, 0.., e_B / gamma); z = T^-1 u and xi = 1 / (1 + v.z) are FP64.  Not
+// inlined, so the single-plan and multi-plan kernels run the same code.
+template <typename C>
+__device__ __noinline__ void azimuth_system(const SetupBArgs<C>& A, int j) {
+    const int steps = A.steps, Nt = A.Nt, NtP = A.NtP, periodic = A.periodic;
+    const double k0 = A.k0, dr = A.dr, dtheta = A.dtheta, r0 = A.r0;
+    C* __restrict__ mB = A.mB;
+    C* __restrict__ zsm = A.zsm;
+    double2* __restrict__ gscr = A.gscr;
+    StepConst* __restrict__ sc = A.sc;
+    int* status = A.status;
+    const int hk_stride = A.hk_stride, y_mid = A.y_mid;
     const double kd = k0 * dr;
     const double rs = r0 + (double)(j + 1) * dr;                 // the field's range after step j
     const double back = y_mid ? 0.5 : 0.0;                       // Y at r_{j+1}, or at the midpoint
@@ -1165,6 +1226,26 @@ __global__ void k_setupB(int steps, int Nt, int NtP, int periodic, double k0, do
     }
     sc[j] = out;
     if (bad) atomicExch(status, ST_SINGULAR);
+}
+
+template <typename C>
+__global__ void k_setupB(int steps, int Nt, int NtP, int periodic, double k0, double dr, double dtheta,
+                         double r0, C* __restrict__ mB, C* __restrict__ zsm, double2* __restrict__ gscr,
+                         StepConst* __restrict__ sc, int* status, int hk_stride, int y_mid) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= steps) return;
+    const SetupBArgs<C> A{steps, Nt, NtP, periodic, k0, dr, dtheta, r0, mB, zsm, gscr, sc, status, hk_stride, y_mid};
+    azimuth_system<C>(A, j);
+}
+
+// The azimuth set-up of n plans in one launch (thread per plan and step;
+// prefix[i] = steps of plans before i).
+template <typename C>
+__global__ void k_setupB_multi(const SetupBArgs<C>* __restrict__ a, const int* __restrict__ prefix, int n) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= prefix[n]) return;
+    const int i = owner_of(prefix, n, idx);
+    azimuth_system<C>(a[i], idx - prefix[i]);
 }
 
 }  // namespace pe3d

@@ -1,5 +1,6 @@
 // pe3d_march_impl.cuh -- typed host launch layer (included once per precision).
 #pragma once
+#include <cstring>
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -286,11 +287,76 @@ int interp_setup(pe3d_plan_s* p, int j_first, int count, int ring, cudaStream_t 
     return PE3D_OK;
 }
 
+// Upload `bytes` of host data to the owner's set-up descriptor buffer (grown
+// as needed; the previous launch that read it is ordered before on the stream)
+inline int upload_setupbuf(pe3d_plan_s* owner, const void* host, size_t bytes) {
+    if (bytes > owner->setupbuf_bytes) {
+        dev_free(owner, &owner->setupbuf, owner->setupbuf_bytes);
+        owner->setupbuf_bytes = 0;
+        int rc = dev_alloc(owner, &owner->setupbuf, bytes);
+        if (rc) return rc;
+        owner->setupbuf_bytes = bytes;
+    }
+    PE3D_CUDA(cudaMemcpyAsync(owner->setupbuf, host, bytes, cudaMemcpyHostToDevice, owner->stream));
+    return PE3D_OK;
+}
+
+// Launch `kern` over n descriptors D and their work counts: one thread per
+// work item, the items of plan i numbered from prefix[i]
+template <typename D>
+int launch_multi(pe3d_plan_s* owner, const std::vector<D>& descs, const std::vector<int>& counts,
+                 void (*kern)(const D*, const int*, int)) {
+    const int n = (int)descs.size();
+    if (n == 0) return PE3D_OK;
+    std::vector<int> prefix(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        if ((long long)prefix[i] + counts[i] > INT_MAX) return fail(PE3D_ERR_ARG, "multi-plan set-up too large");
+        prefix[i + 1] = prefix[i] + counts[i];
+    }
+    if (prefix[n] == 0) return PE3D_OK;
+    const size_t db = (sizeof(D) * n + 15) & ~size_t(15);
+    std::vector<unsigned char> host(db + sizeof(int) * (n + 1));
+    std::memcpy(host.data(), descs.data(), sizeof(D) * n);
+    std::memcpy(host.data() + db, prefix.data(), sizeof(int) * (n + 1));
+    int rc = upload_setupbuf(owner, host.data(), host.size());
+    if (rc) return rc;
+    const D* dd = reinterpret_cast<const D*>(owner->setupbuf);
+    const int* dp = reinterpret_cast<const int*>(reinterpret_cast<const unsigned char*>(owner->setupbuf) + db);
+    kern<<<(prefix[n] + 127) / 128, 128, 0, owner->stream>>>(dd, dp, n);
+    PE3D_CUDA(cudaGetLastError());
+    owner->total_launches += 1;
+    return PE3D_OK;
+}
+
+// The depth set-up (per-slice multipliers) of n plans in one launch
+template <typename C>
+int setupA_multi(pe3d_plan_s* const* plans, int n) {
+    std::vector<SetupADesc<C>> d;
+    std::vector<int> counts;
+    for (int i = 0; i < n; ++i) {
+        pe3d_plan_s* p = plans[i];
+        const DepthConsts dc = depth_consts(p);
+        d.push_back(SetupADesc<C>{reinterpret_cast<const double2*>(p->n2), reinterpret_cast<C*>(p->mz), p->status,
+                                  p->Nz, p->ldz, dc.alpha, dc.einv, dc.s});
+        counts.push_back(p->nslices * p->Nt);
+    }
+    return launch_multi<SetupADesc<C>>(plans[0], d, counts, k_setupA_multi<C>);
+}
+
+// arguments of the azimuth set-up of one march
+template <typename C>
+SetupBArgs<C> setupB_args(pe3d_plan_s* p, double r0, int steps, int stride) {
+    return SetupBArgs<C>{steps, p->Nt, p->NtP, p->boundary == PE3D_PERIODIC, p->k0, p->dr, p->dtheta, r0,
+                         reinterpret_cast<C*>(p->mB), reinterpret_cast<C*>(p->zsm),
+                         reinterpret_cast<double2*>(p->gscr), reinterpret_cast<StepConst*>(p->sc), p->status,
+                         p->out_mode != PE3D_OUT_FIELD ? stride : 0, p->y_mid};
+}
+
 // per-step setup (FP64 azimuth pivots and step constants) + the slice table.
 // An interpolated medium's depth systems of every step are set up here too
 // (step j's in slot j).
 template <typename C>
-int step_setup(pe3d_plan_s* p, double r0, int steps, int stride) {
+int step_setup(pe3d_plan_s* p, double r0, int steps, int stride, bool launch_b = true) {
     int rc = ensure_steps(p, steps);
     if (rc) return rc;
     std::vector<int> sos(steps);
@@ -315,10 +381,11 @@ int step_setup(pe3d_plan_s* p, double r0, int steps, int stride) {
         for (int j = 0; j < steps; ++j) sos[j] = active_slice(p->slice_r, r0 + (double)(j + 1) * p->dr);
     }
     PE3D_CUDA(cudaMemcpyAsync(p->slice_of_step, sos.data(), sizeof(int) * steps, cudaMemcpyHostToDevice, p->stream));
+    if (!launch_b) return PE3D_OK;        // the caller sets the azimuth systems up (k_setupB_multi)
+    const SetupBArgs<C> a = setupB_args<C>(p, r0, steps, stride);
     k_setupB<C><<<(steps + 127) / 128, 128, 0, p->stream>>>(
-        steps, p->Nt, p->NtP, p->boundary == PE3D_PERIODIC, p->k0, p->dr, p->dtheta, r0,
-        reinterpret_cast<C*>(p->mB), reinterpret_cast<C*>(p->zsm), reinterpret_cast<double2*>(p->gscr),
-        reinterpret_cast<StepConst*>(p->sc), p->status, p->out_mode != PE3D_OUT_FIELD ? stride : 0, p->y_mid);
+        a.steps, a.Nt, a.NtP, a.periodic, a.k0, a.dr, a.dtheta, a.r0, a.mB, a.zsm, a.gscr, a.sc, a.status,
+        a.hk_stride, a.y_mid);
     PE3D_CUDA(cudaGetLastError());
     return PE3D_OK;
 }

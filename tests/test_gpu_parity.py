@@ -384,9 +384,50 @@ def test_batch_of_more_than_64_marches(P):
     P.pe3d_march_batched([p.h for p in plans], u0s, [wl.grid.r0 for wl in wls], [wl.grid.steps for wl in wls],
                          [1] * len(wls), outs)
     torch.cuda.synchronize()
-    assert P.pe3d_plan_info(plans[0].h)["launches"] == 2 + 2 * len(wls)
+    # two batched launches, a prologue per march, one azimuth set-up for all
+    assert P.pe3d_plan_info(plans[0].h)["launches"] == 2 + len(wls) + 1
     for i in (0, 1, 63, 64, 69):
         alone, _ = gpu_march(P, wls[i], fp32=True)
         assert np.array_equal(outs[i].cpu().numpy(), alone)
     for pl in plans:
         pl.close()
+
+
+@pytest.mark.parametrize("fp32", [False, True], ids=["fp64", "fp32"])
+def test_set_medium_batched(P, fp32):
+    """One depth set-up launch for many plans leaves each plan as its own
+    pe3d_set_medium would: every march is bit-identical, also for a plan with
+    an interpolated medium and for media given in host memory."""
+    specs = [(300, 70, False, 3), (37, 257, True, 2), (1067, 16, False, 5), (5, 3, True, 1)]
+    wls = [workloads.random_case(Nz, Nt, periodic=per, K=K, steps=4, seed=400 + i, stride=2)
+           for i, (Nz, Nt, per, K) in enumerate(specs)]
+    interp = [False, False, True, False]
+    ref = [gpu_march(P, wl, fp32=fp32, interp=it)[0] for wl, it in zip(wls, interp)]
+    for on_device in (True, False):
+        plans = [P.Plan.for_grid(wl.grid, fp32=fp32, interp=it) for wl, it in zip(wls, interp)]
+        n2s = [torch.from_numpy(wl.n2).cuda() if on_device else wl.n2 for wl in wls]
+        P.pe3d_set_medium_batched([pl.h for pl in plans], n2s, [wl.slice_r for wl in wls])
+        cdt = np.complex64 if fp32 else np.complex128
+        for pl, wl, r in zip(plans, wls, ref):
+            got = pl.march(torch.from_numpy(wl.u0.astype(cdt)).cuda(), wl.grid.r0, wl.grid.steps, wl.grid.stride)
+            assert np.array_equal(got.cpu().numpy(), r)
+        for pl in plans:
+            pl.close()
+
+
+def test_set_medium_batched_errors(P):
+    wl = workloads.random_case(20, 5, periodic=False, K=1, steps=1, seed=9)
+    a = P.Plan.for_grid(wl.grid, fp32=True)
+    b = P.Plan.for_grid(wl.grid, fp32=False)
+    n2 = torch.from_numpy(wl.n2).cuda()
+    with pytest.raises(P.PE3DError) as e:
+        P.pe3d_set_medium_batched([a.h, b.h], [n2, n2], [wl.slice_r, wl.slice_r])
+    assert e.value.code == P.PE3D_ERR_ARG
+    with pytest.raises(P.PE3DError) as e:
+        P.pe3d_set_medium_batched([a.h, a.h], [n2, n2], [wl.slice_r, wl.slice_r])
+    assert e.value.code == P.PE3D_ERR_ARG
+    with pytest.raises(P.PE3DError) as e:                 # march before any medium
+        a.march(torch.zeros((5, 20), dtype=torch.complex64, device="cuda"), 100.0, 1, 1)
+    assert e.value.code == P.PE3D_ERR_STATE
+    a.close()
+    b.close()
