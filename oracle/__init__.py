@@ -57,9 +57,11 @@ class OracleLib:
         P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
         L.oracle_tridiag_solve.argtypes = [I, P, P, P, P]
         L.oracle_cyclic_solve.argtypes = [I, P, P, P, P]
-        L.oracle_step.argtypes = [I, I, D, D, D, D, D, I, P, P, I]
-        L.oracle_march.argtypes = [I, I, D, D, D, D, I, P, P, I, P, D, I, I, P, I, I, I]
-        for f in ("oracle_tridiag_solve", "oracle_cyclic_solve", "oracle_step", "oracle_march"):
+        L.oracle_step.argtypes = [I, I, D, D, D, D, D, I, P, P, I, I]
+        L.oracle_march.argtypes = [I, I, D, D, D, D, I, P, P, I, P, D, I, I, P, I, I, I, I]
+        L.oracle_penta_solve.argtypes = [I, P, P]
+        for f in ("oracle_tridiag_solve", "oracle_cyclic_solve", "oracle_step", "oracle_march",
+                  "oracle_penta_solve"):
             getattr(L, f).restype = I
         self.L = L
 
@@ -85,18 +87,28 @@ class OracleLib:
             raise RuntimeError(f"oracle_cyclic_solve failed ({rc})")
         return x
 
-    def step(self, u, n2, *, dz, dtheta, dr, k0, rstar, periodic, nthreads=1):
+    def penta_solve(self, bands, b):
+        """Solve with the oracle's banded elimination: bands [n][5] hold row i's
+        columns i-2 .. i+2."""
+        bands = self._c128(bands)
+        x = self._c128(b).copy()
+        rc = self.L.oracle_penta_solve(len(x), bands.ctypes.data, x.ctypes.data)
+        if rc:
+            raise RuntimeError(f"oracle_penta_solve failed ({rc})")
+        return x
+
+    def step(self, u, n2, *, dz, dtheta, dr, k0, rstar, periodic, nthreads=1, taylor=False):
         u = self._c128(u).copy()
         n2 = self._c128(n2)
         Nt, Nz = u.shape
         rc = self.L.oracle_step(Nz, Nt, dz, dtheta, dr, k0, rstar, int(periodic),
-                                n2.ctypes.data, u.ctypes.data, int(nthreads))
+                                n2.ctypes.data, u.ctypes.data, int(nthreads), int(bool(taylor)))
         if rc:
             raise RuntimeError(f"oracle_step failed ({rc})")
         return u
 
     def march(self, grid, n2, slice_r, u0, *, steps=None, stride=None, r0=None, nthreads=None,
-              y_midpoint=False, interp=False):
+              y_midpoint=False, interp=False, taylor=False):
         steps = grid.steps if steps is None else steps
         stride = grid.stride if stride is None else stride
         r0 = grid.r0 if r0 is None else r0
@@ -110,7 +122,7 @@ class OracleLib:
         rc = self.L.oracle_march(Nz, Nt, grid.dz, grid.dtheta, grid.dr, grid.k0, int(grid.periodic),
                                  n2.ctypes.data, slice_r.ctypes.data, len(slice_r), u0.ctypes.data,
                                  float(r0), int(steps), int(stride), out.ctypes.data, int(nthreads),
-                                 int(bool(y_midpoint)), int(bool(interp)))
+                                 int(bool(y_midpoint)), int(bool(interp)), int(bool(taylor)))
         if rc:
             raise RuntimeError(f"oracle_march failed ({rc})")
         return out[:n_out]

@@ -203,10 +203,98 @@ static cplx theta_nb(const cplx *u, int Nz, int Nt, int periodic, int m, int dm,
     return u[(size_t)mm * Nz + l];
 }
 
+/* Row l of X^2, the square of the discrete X with its zero ghosts, as the
+ * bands at columns l-2 .. l+2 (x2[0..4]): X's row l times X's columns.     */
+static void x2_row(const cplx *n2_m, int Nz, double s, int l, cplx x2[5])
+{
+    for (int b = 0; b < 5; ++b) x2[b] = 0.0;
+    cplx lo, mid, hi;
+    x_row(n2_m, Nz, s, l, &lo, &mid, &hi);
+    for (int k = l - 1; k <= l + 1; ++k) {
+        if (k < 0 || k >= Nz) continue;
+        const cplx xlk = (k == l - 1) ? lo : (k == l) ? mid : hi;    /* X[l][k] */
+        cplx klo, kmid, khi;
+        x_row(n2_m, Nz, s, k, &klo, &kmid, &khi);
+        if (k - 1 >= 0) x2[(k - 1) - l + 2] += xlk * klo;           /* X[k][k-1] */
+        x2[k - l + 2] += xlk * kmid;                                 /* X[k][k]   */
+        if (k + 1 < Nz) x2[(k + 1) - l + 2] += xlk * khi;           /* X[k][k+1] */
+    }
+}
+
+/* Banded Gaussian elimination with partial pivoting (row interchanges) for
+ * an n x n system with kl = 2 sub- and ku = 2 superdiagonals, the textbook
+ * band algorithm: ab holds column j of the matrix at ab[(KV + i - j) + j * LDAB]
+ * for rows i in j-ku .. j+kl, with KV = kl + ku rows of room above for the
+ * fill that interchanges cause.  On return ab holds the factors; b (length
+ * n) is overwritten with x.  ipiv: n ints of work.                         */
+enum { PB_KL = 2, PB_KU = 2, PB_KV = 4, PB_LDAB = 7 };
+static int penta_gepp(int n, cplx *ab, cplx *b, int *ipiv)
+{
+#define AB(r, c) ab[(r) + (size_t)(c) * PB_LDAB]
+    int ju = 0;
+    for (int j = 0; j < n; ++j) {
+        const int km = (PB_KL < n - 1 - j) ? PB_KL : n - 1 - j;
+        int p = 0;
+        double best = cabs(AB(PB_KV, j));
+        for (int t = 1; t <= km; ++t)
+            if (cabs(AB(PB_KV + t, j)) > best) { best = cabs(AB(PB_KV + t, j)); p = t; }
+        ipiv[j] = j + p;
+        if (AB(PB_KV + p, j) == 0.0) return OR_ERR_SINGULAR;
+        const int jr = (j + PB_KU + p < n - 1) ? j + PB_KU + p : n - 1;
+        if (jr > ju) ju = jr;
+        if (p != 0)
+            for (int c = j; c <= ju; ++c) {      /* swap rows j and j+p in columns j..ju */
+                const cplx t = AB(PB_KV + j - c, c);
+                AB(PB_KV + j - c, c) = AB(PB_KV + j + p - c, c);
+                AB(PB_KV + j + p - c, c) = t;
+            }
+        for (int t = 1; t <= km; ++t) AB(PB_KV + t, j) = AB(PB_KV + t, j) / AB(PB_KV, j);
+        for (int c = j + 1; c <= ju; ++c)        /* rows j+1..j+km of columns j+1..ju */
+            for (int t = 1; t <= km; ++t)
+                AB(PB_KV + j + t - c, c) = AB(PB_KV + j + t - c, c) - AB(PB_KV + t, j) * AB(PB_KV + j - c, c);
+    }
+    for (int j = 0; j < n; ++j) {                /* L y = P b */
+        const int km = (PB_KL < n - 1 - j) ? PB_KL : n - 1 - j;
+        if (ipiv[j] != j) { const cplx t = b[j]; b[j] = b[ipiv[j]]; b[ipiv[j]] = t; }
+        for (int t = 1; t <= km; ++t) b[j + t] = b[j + t] - AB(PB_KV + t, j) * b[j];
+    }
+    for (int j = n - 1; j >= 0; --j) {           /* U x = y, U with KV superdiagonals */
+        b[j] = b[j] / AB(PB_KV, j);
+        const int i0 = (j - PB_KV > 0) ? j - PB_KV : 0;
+        for (int i = i0; i < j; ++i) b[i] = b[i] - AB(PB_KV + i - j, j) * b[j];
+    }
+    return OR_OK;
+#undef AB
+}
+
+/* The banded solver on its own (for its pins): row i of the system holds
+ * columns i-2 .. i+2 in bands[5 i .. 5 i + 4] (entries outside the matrix
+ * are ignored); b is overwritten with x.                                   */
+int oracle_penta_solve(int n, const cplx *bands, cplx *b)
+{
+    if (n <= 0) return OR_ERR_ARG;
+    cplx *ab = (cplx *)calloc((size_t)PB_LDAB * n, sizeof(cplx));
+    int *ipiv = (int *)malloc(sizeof(int) * (size_t)n);
+    if (!ab || !ipiv) { free(ab); free(ipiv); return OR_ERR_OOM; }
+    for (int i = 0; i < n; ++i)
+        for (int q = 0; q < 5; ++q) {
+            const int col = i - 2 + q;
+            if (col >= 0 && col < n) ab[(PB_KV + i - col) + (size_t)col * PB_LDAB] = bands[5 * (size_t)i + q];
+        }
+    int rc = penta_gepp(n, ab, b, ipiv);
+    free(ab);
+    free(ipiv);
+    return rc;
+}
+
 /* One range step r_j -> r_j + dr, all operators evaluated at r* (Eq. 4-8).
- * u: [Nt][Nz] in/out.  n2: [Nt][Nz] slice active at r*.                   */
+ * u: [Nt][Nz] in/out.  n2: [Nt][Nz] slice active at r*.
+ * With taylor, the depth factors are those of Eq. 3's Taylor form
+ * sqrt(1 + x) ~ 1 + x/2 - x^2/8 under the same Crank-Nicolson split:
+ * [1 - (d/2)(X/2 - X^2/8)] on the left, [1 + (d/2)(X/2 - X^2/8)] on the right,
+ * pentadiagonal in depth; the azimuth factors are unchanged.              */
 int oracle_step(int Nz, int Nt, double dz, double dtheta, double dr, double k0,
-                double rstar, int periodic, const cplx *n2, cplx *u, int nthreads)
+                double rstar, int periodic, const cplx *n2, cplx *u, int nthreads, int taylor)
 {
     if (Nz <= 0 || Nt <= 0 || !(k0 > 0.0) || !(dz > 0.0) || !(dtheta > 0.0) || rstar <= 0.0)
         return OR_ERR_ARG;
@@ -236,6 +324,51 @@ int oracle_step(int Nz, int Nt, double dz, double dtheta, double dr, double k0,
             w[(size_t)m * Nz + l] = u[(size_t)m * Nz + l] + yfac * yu;
         }
 
+    /* 2-3 (Taylor form). per azimuth: RHS = [1 + (d/4) X - (d/16) X^2] w, then
+     * solve [1 - (d/4) X + (d/16) X^2] v = RHS (pentadiagonal, banded GEPP) */
+    if (taylor) {
+#pragma omp parallel num_threads(nthreads)
+        {
+            cplx *ab = (cplx *)calloc((size_t)PB_LDAB * Nz + Nz, sizeof(cplx));
+            int *ipiv = (int *)malloc(sizeof(int) * (size_t)Nz);
+            if (!ab || !ipiv) {
+#pragma omp atomic write
+                status = OR_ERR_OOM;
+            } else {
+                cplx *rhs = ab + (size_t)PB_LDAB * Nz;
+#pragma omp for schedule(static)
+                for (int m = 0; m < Nt; ++m) {
+                    const cplx *n2m = n2 + (size_t)m * Nz;
+                    const cplx *wm = w + (size_t)m * Nz;
+                    memset(ab, 0, sizeof(cplx) * (size_t)PB_LDAB * Nz);
+                    for (int l = 0; l < Nz; ++l) {
+                        cplx lo, mid, hi, x2[5];
+                        x_row(n2m, Nz, s, l, &lo, &mid, &hi);
+                        x2_row(n2m, Nz, s, l, x2);
+                        const cplx xr[5] = {0.0, lo, mid, hi, 0.0};
+                        cplx xw = 0.0, x2w = 0.0;
+                        for (int b = 0; b < 5; ++b) {
+                            const int col = l - 2 + b;
+                            if (col < 0 || col >= Nz) continue;
+                            xw = xw + xr[b] * wm[col];
+                            x2w = x2w + x2[b] * wm[col];
+                            const cplx a = (b == 2 ? 1.0 : 0.0) - (delta / 4.0) * xr[b] + (delta / 16.0) * x2[b];
+                            ab[(PB_KV + l - col) + (size_t)col * PB_LDAB] = a;
+                        }
+                        rhs[l] = wm[l] + (delta / 4.0) * xw - (delta / 16.0) * x2w;
+                    }
+                    int rc = penta_gepp(Nz, ab, rhs, ipiv);
+                    if (rc) {
+#pragma omp atomic write
+                        status = rc;
+                    }
+                    memcpy(v + (size_t)m * Nz, rhs, sizeof(cplx) * Nz);
+                }
+            }
+            free(ab);
+            free(ipiv);
+        }
+    } else
     /* 2-3. per azimuth: RHS = [1 + beta X] w, then solve [1 + alpha X] v = RHS */
 #pragma omp parallel num_threads(nthreads)
     {
@@ -343,10 +476,11 @@ static void interpolated_medium(const cplx *n2, const double *slice_r, int K, si
  * (Fig. 2 advances r before updating A and B), or, with y_midpoint, at the
  * step's midpoint r0 + (j + 1/2) dr (the centred variant of the scheme).
  * With interp, the medium of step j is n^2 interpolated linearly in range at
- * r* (interpolated_medium) instead of the active slice.                   */
+ * r* (interpolated_medium) instead of the active slice.  With taylor, every
+ * step takes the Taylor form of the depth factors (see oracle_step).      */
 int oracle_march(int Nz, int Nt, double dz, double dtheta, double dr, double k0, int periodic,
                  const cplx *n2, const double *slice_r, int K, const cplx *u0, double r0,
-                 int steps, int stride, cplx *out, int nthreads, int y_midpoint, int interp)
+                 int steps, int stride, cplx *out, int nthreads, int y_midpoint, int interp, int taylor)
 {
     if (Nz <= 0 || Nt <= 0 || K <= 0 || steps < 0 || stride <= 0 || r0 <= 0.0) return OR_ERR_ARG;
     size_t npts = (size_t)Nz * Nt;
@@ -369,7 +503,7 @@ int oracle_march(int Nz, int Nt, double dz, double dtheta, double dr, double k0,
         } else {
             n2j = n2 + (size_t)active_slice(slice_r, K, rstar) * npts;
         }
-        rc = oracle_step(Nz, Nt, dz, dtheta, dr, k0, ry, periodic, n2j, u, nthreads);
+        rc = oracle_step(Nz, Nt, dz, dtheta, dr, k0, ry, periodic, n2j, u, nthreads, taylor);
         if (rc == OR_OK && (j + 1) % stride == 0)
             memcpy(out + (size_t)((j + 1) / stride - 1) * npts, u, sizeof(cplx) * npts);
     }

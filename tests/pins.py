@@ -54,14 +54,21 @@ def dense_operators(n2_slice, grid, rstar):
     return X, Y
 
 
-def dense_step(u, n2_slice, grid, rstar, dr=None):
-    """u^{j+1} = solve([1+(1/4-d/4)X][1-(d/4)Y], [1+(1/4+d/4)X][1+(d/4)Y] u^j)."""
+def dense_step(u, n2_slice, grid, rstar, dr=None, taylor=False):
+    """u^{j+1} = solve([1+(1/4-d/4)X][1-(d/4)Y], [1+(1/4+d/4)X][1+(d/4)Y] u^j) (Eq. 4),
+    or with the Taylor form of Eq. 3, T = X/2 - X^2/8:
+    solve([1-(d/2)T][1-(d/4)Y], [1+(d/2)T][1+(d/4)Y] u^j)."""
     dr = grid.dr if dr is None else dr
     d = 1j * grid.k0 * dr
     X, Y = dense_operators(n2_slice, grid, rstar)
     Id = np.eye(X.shape[0])
-    lhs = (Id + (0.25 - d / 4) * X) @ (Id - (d / 4) * Y)
-    rhs = (Id + (0.25 + d / 4) * X) @ (Id + (d / 4) * Y)
+    if taylor:
+        T = X / 2 - (X @ X) / 8
+        lhs = (Id - (d / 2) * T) @ (Id - (d / 4) * Y)
+        rhs = (Id + (d / 2) * T) @ (Id + (d / 4) * Y)
+    else:
+        lhs = (Id + (0.25 - d / 4) * X) @ (Id - (d / 4) * Y)
+        rhs = (Id + (0.25 + d / 4) * X) @ (Id + (d / 4) * Y)
     return np.linalg.solve(lhs, rhs @ u.ravel()).reshape(u.shape)
 
 
@@ -78,15 +85,15 @@ def y_range(g, j, y_midpoint):
     return g.r0 + (j + 0.5) * g.dr if y_midpoint else g.r0 + (j + 1) * g.dr
 
 
-def check_dense(lib, periodic: bool, seed: int = 3, y_midpoint: bool = False) -> float:
+def check_dense(lib, periodic: bool, seed: int = 3, y_midpoint: bool = False, taylor: bool = False) -> float:
     wl = workloads.random_case(6, 5, periodic=periodic, K=3, steps=5, seed=seed, stride=1)
     g = wl.grid
-    got = lib.march(g, wl.n2, wl.slice_r, wl.u0, y_midpoint=y_midpoint)
+    got = lib.march(g, wl.n2, wl.slice_r, wl.u0, y_midpoint=y_midpoint, taylor=taylor)
     u = wl.u0.copy()
     err = 0.0
     for j in range(g.steps):
         rstar = g.r0 + (j + 1) * g.dr
-        u = dense_step(u, wl.n2[active_slice(wl.slice_r, rstar)], g, y_range(g, j, y_midpoint))
+        u = dense_step(u, wl.n2[active_slice(wl.slice_r, rstar)], g, y_range(g, j, y_midpoint), taylor=taylor)
         err = max(err, relerr(got[j], u))
     return err
 
@@ -121,7 +128,7 @@ def check_interp_linear(lib, periodic: bool, y_midpoint: bool = False) -> float:
 # --------------------------------------------------------------------------
 
 def check_eigenmodes(lib, periodic: bool, n0sq: float, q: int = 2, p: int = 1,
-                     steps: int = 7, y_midpoint: bool = False) -> float:
+                     steps: int = 7, y_midpoint: bool = False, taylor: bool = False) -> float:
     Nz, Nt = 9, 8
     g = workloads.Grid(Nz=Nz, Ntheta=Nt, dz=3.0, dtheta=(2 * math.pi / Nt) if periodic else 0.05,
                        dr=7.0, k0=0.3, r0=40.0, steps=steps, stride=steps, periodic=periodic)
@@ -136,7 +143,7 @@ def check_eigenmodes(lib, periodic: bool, n0sq: float, q: int = 2, p: int = 1,
         mu_unit = -4.0 * math.sin((p + 1) * math.pi / (2 * (Nt + 1))) ** 2
     u0 = (tmode[:, None] * zmode[None, :]).astype(np.complex128)
     n2 = np.full((1, Nt, Nz), n0sq, np.complex128)
-    got = lib.march(g, n2, np.array([g.r0]), u0, y_midpoint=y_midpoint)[-1]
+    got = lib.march(g, n2, np.array([g.r0]), u0, y_midpoint=y_midpoint, taylor=taylor)[-1]
     d = 1j * g.k0 * g.dr
     s = 1.0 / (g.k0 * g.dz) ** 2
     lam = (n0sq - 1.0) - 4.0 * s * math.sin((q + 1) * math.pi / (2 * (Nz + 1))) ** 2
@@ -145,7 +152,11 @@ def check_eigenmodes(lib, periodic: bool, n0sq: float, q: int = 2, p: int = 1,
     for j in range(steps):
         c = 1.0 / (g.k0 * y_range(g, j, y_midpoint) * g.dtheta) ** 2
         mu = c * mu_unit
-        gain *= (1 + beta * lam) / (1 + alpha * lam) * (1 + d / 4 * mu) / (1 - d / 4 * mu)
+        if taylor:     # X's eigenvalue lam gives T = lam/2 - lam^2/8
+            tl = lam / 2 - lam * lam / 8
+            gain *= (1 + d / 2 * tl) / (1 - d / 2 * tl) * (1 + d / 4 * mu) / (1 - d / 4 * mu)
+        else:
+            gain *= (1 + beta * lam) / (1 + alpha * lam) * (1 + d / 4 * mu) / (1 - d / 4 * mu)
     return relerr(got, gain * u0)
 
 
@@ -153,14 +164,14 @@ def check_eigenmodes(lib, periodic: bool, n0sq: float, q: int = 2, p: int = 1,
 # invariants
 # --------------------------------------------------------------------------
 
-def check_norm_conservation(lib, periodic: bool, steps: int = 40) -> float:
+def check_norm_conservation(lib, periodic: bool, steps: int = 40, taylor: bool = False) -> float:
     """Real, theta-independent n^2 (depth- and range-dependent): X and Y commute
     and both factors are Cayley transforms, so ||u|| is conserved exactly."""
     rng = np.random.default_rng(11)
     Nz, Nt, K = 13, 7, 4
     wl = workloads.random_case(Nz, Nt, periodic=periodic, K=K, steps=steps, seed=11,
                                lossy=False, theta_dependent=False, stride=1)
-    got = lib.march(wl.grid, wl.n2, wl.slice_r, wl.u0)
+    got = lib.march(wl.grid, wl.n2, wl.slice_r, wl.u0, taylor=taylor)
     n0 = np.linalg.norm(wl.u0)
     worst = 0.0
     for j in range(steps):
@@ -224,6 +235,27 @@ def check_tridiag(lib, seed: int = 1) -> float:
     return worst
 
 
+def check_penta(lib, seed: int = 6) -> float:
+    """The banded (kl = ku = 2) elimination against LAPACK, including systems
+    whose small diagonal forces row interchanges."""
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    for n in (1, 2, 3, 4, 7, 40):
+        for weak in (False, True):
+            bands = rng.normal(size=(n, 5)) + 1j * rng.normal(size=(n, 5))
+            if weak:
+                bands[:, 2] *= 1e-3
+            A = np.zeros((n, n), np.complex128)
+            for i in range(n):
+                for q in range(5):
+                    c = i - 2 + q
+                    if 0 <= c < n:
+                        A[i, c] = bands[i, q]
+            b = rng.normal(size=n) + 1j * rng.normal(size=n)
+            worst = max(worst, relerr(lib.penta_solve(bands, b), np.linalg.solve(A, b)))
+    return worst
+
+
 def check_cyclic_fft(lib, seed: int = 2) -> float:
     """Constant-coefficient cyclic system = circulant: x = ifft(fft(b) / eig),
     eig_p = d + 2 e cos(2 pi p / n)."""
@@ -274,6 +306,13 @@ ALL_CHECKS = {
     "interp_walled": lambda L: check_interp_linear(L, periodic=False),
     "interp_periodic": lambda L: check_interp_linear(L, periodic=True),
     "interp_walled_mid": lambda L: check_interp_linear(L, periodic=False, y_midpoint=True),
+    # the Taylor form of Eq. 3
+    "dense_walled_taylor": lambda L: check_dense(L, periodic=False, taylor=True),
+    "dense_periodic_taylor": lambda L: check_dense(L, periodic=True, taylor=True),
+    "eig_walled_taylor": lambda L: check_eigenmodes(L, False, 0.9, taylor=True),
+    "eig_periodic_taylor": lambda L: check_eigenmodes(L, True, 0.9, taylor=True),
+    "norm_walled_taylor": lambda L: check_norm_conservation(L, False, taylor=True),
+    "penta": check_penta,
     "norm_walled": lambda L: check_norm_conservation(L, False),
     "norm_periodic": lambda L: check_norm_conservation(L, True),
     "reverse_walled": lambda L: check_reversibility(L, False),
@@ -289,3 +328,5 @@ ALL_CHECKS = {
 TOLS = {k: TOL for k in ALL_CHECKS}
 TOLS["norm_walled"] = 1e-13
 TOLS["norm_periodic"] = 1e-13
+TOLS["norm_walled_taylor"] = 1e-13
+TOLS["penta"] = 1e-10         # weak-diagonal systems have condition numbers near 1e3

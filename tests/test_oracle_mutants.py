@@ -42,6 +42,15 @@ MUTANTS = {
     "interp_same_slice": ("*b = n2 + (size_t)(k + 1) * npts;", "*b = n2 + (size_t)k * npts;"),
     "interp_ignored": ("        if (interp) {", "        if (0) {"),
     "interp_hold_first": ("if (k + 1 >= K || r < slice_r[k]) {", "if (k + 1 >= K) {"),
+    # the Taylor form of Eq. 3 and its banded solve
+    "taylor_x2_sign": ("- (delta / 4.0) * xr[b] + (delta / 16.0) * x2[b];", "- (delta / 4.0) * xr[b] - (delta / 16.0) * x2[b];"),
+    "taylor_drop_x2_rhs": ("rhs[l] = wm[l] + (delta / 4.0) * xw - (delta / 16.0) * x2w;",
+                           "rhs[l] = wm[l] + (delta / 4.0) * xw;"),
+    "x2_wrong_band": ("if (k + 1 < Nz) x2[(k + 1) - l + 2] += xlk * khi;", "if (k + 1 < Nz) x2[(k + 1) - l + 2] += xlk * kmid;"),
+    "penta_no_interchange": ("        if (p != 0)\n            for (int c = j; c <= ju; ++c) {",
+                             "        if (0)\n            for (int c = j; c <= ju; ++c) {"),
+    "penta_forward_sign": ("for (int t = 1; t <= km; ++t) b[j + t] = b[j + t] - AB(PB_KV + t, j) * b[j];",
+                           "for (int t = 1; t <= km; ++t) b[j + t] = b[j + t] + AB(PB_KV + t, j) * b[j];"),
     # solvers
     "backsub_index": ("- u2[i] * b[i + 2]) / d[i];", "- u2[i] * b[i + 1]) / d[i];"),
     "swap_fill_sign": ("if (i + 2 < n) u1[i + 1] = 0.0 - mult * r_i2;",
