@@ -202,19 +202,23 @@ WORKLOADS = {
     "walled-50Hz": ("fp64", lambda: workloads.config1()),
     "periodic-200Hz": ("fp32", lambda: workloads.config3()),
     "medium-100Hz-interp": ("fp32", lambda: workloads.config2()),
+    "medium-100Hz-taylor": ("fp32", lambda: workloads.config2()),
 }
+# workloads marched with the Taylor form of Eq. 3 (stream launches)
+TAYLOR_WORKLOADS = {"medium-100Hz-taylor"}
 # workloads whose n^2 is interpolated linearly in range, with the FP64 depth
 # systems set up for every range step
 INTERP_WORKLOADS = {"medium-100Hz-interp"}
 
 
-def oracle_run(wl, steps: int, nthreads: int, interp: bool = False):
+def oracle_run(wl, steps: int, nthreads: int, interp: bool = False, taylor: bool = False):
     import oracle
     L = oracle.load()
     g = wl.grid
     stride = g.stride if steps % g.stride == 0 else steps
     t = time.perf_counter()
-    out = L.march(g, wl.n2, wl.slice_r, wl.u0, steps=steps, stride=stride, nthreads=nthreads, interp=interp)
+    out = L.march(g, wl.n2, wl.slice_r, wl.u0, steps=steps, stride=stride, nthreads=nthreads, interp=interp,
+                  taylor=taylor)
     return out, time.perf_counter() - t
 
 
@@ -236,11 +240,12 @@ def run_reference(args):
     cores = oracle.default_threads()
     sample_steps = min(g.steps, args.ref_sample_steps)
     interp = args.workload in INTERP_WORKLOADS
+    taylor = args.workload in TAYLOR_WORKLOADS
     for _ in range(args.warmup):
-        oracle_run(wl, sample_steps, cores, interp)
+        oracle_run(wl, sample_steps, cores, interp, taylor)
     times = []
     for _ in range(args.steps):
-        _, dt = oracle_run(wl, sample_steps, cores, interp)
+        _, dt = oracle_run(wl, sample_steps, cores, interp, taylor)
         times.append(dt)
     per = statistics.mean(times)
     value = g.points * sample_steps / per
@@ -248,7 +253,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": g.name + ("-interp" if interp else ""), "sample_range_steps": sample_steps,
+        "config": {"workload": g.name + ("-interp" if interp else "") + ("-taylor" if taylor else ""),
+                   "sample_range_steps": sample_steps,
                    "Nz": g.Nz, "Ntheta": g.Ntheta},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"first {sample_steps} of {g.steps} range steps of {g.name}, "
@@ -276,10 +282,13 @@ def run_ours(args):
     precision, make = WORKLOADS[args.workload]
     fp32 = precision == "fp32"
     interp = args.workload in INTERP_WORKLOADS
+    taylor = args.workload in TAYLOR_WORKLOADS
     wl = make()
     g = wl.grid
     if interp:
         g.name += "-interp"
+    if taylor:
+        g.name += "-taylor"
     if args.range_steps:                      # a truncated march (profiling cases)
         g.steps = min(g.steps, args.range_steps)
         g.stride = max(1, min(g.stride, g.steps))
@@ -293,7 +302,7 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         cores = oracle.default_threads()
-        ref, dt = oracle_run(wl, g.steps, cores, interp)
+        ref, dt = oracle_run(wl, g.steps, cores, interp, taylor)
         cpu = {"value": g.points * g.steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"the full {g.steps}-step march of {g.name} (FP64 C oracle, OpenMP over "
                          f"systems, {dt:.1f} s)"}
@@ -308,7 +317,12 @@ def run_ours(args):
     plan = P.pe3d_plan(g.Nz, g.Ntheta, g.dz, g.dtheta, g.dr, g.k0,
                        P.PE3D_PERIODIC if g.periodic else P.PE3D_WALLED,
                        P.PE3D_FP32 if fp32 else P.PE3D_FP64, stream)
-    P.pe3d_set_option(plan, P.PE3D_OPT_EXEC, args.exec)
+    exec_mode = args.exec
+    if taylor:
+        P.pe3d_set_option(plan, P.PE3D_OPT_SCHEME, P.PE3D_SCHEME_TAYLOR)
+        if exec_mode in (0, 3):         # per-step launches, replayed from one CUDA graph
+            exec_mode = 2
+    P.pe3d_set_option(plan, P.PE3D_OPT_EXEC, exec_mode)
     P.pe3d_set_option(plan, P.PE3D_OPT_TIMING, 1)
     P.pe3d_set_option(plan, P.PE3D_OPT_OUTPUT, out_mode)
     if args.rc:
@@ -383,7 +397,7 @@ def run_ours(args):
 
     # plain FP64 GPU march of the same workload, for comparison
     fp64_value = None
-    if fp32 and not args.no_fp64_compare and not interp:
+    if fp32 and not args.no_fp64_compare and not interp and not taylor:
         u064 = torch.from_numpy(wl.u0).to(dev)
         o64 = torch.empty((g.n_out, g.Ntheta, g.Nz), dtype=torch.complex128, device=dev)
         p64 = P.pe3d_plan(g.Nz, g.Ntheta, g.dz, g.dtheta, g.dr, g.k0,
@@ -410,10 +424,13 @@ def run_ours(args):
         peak, peak_kind = measured_peaks()
         kns = statistics.mean(kernel_ns) if kernel_ns and kernel_ns[0] > 0 else None
         bpp = BYTES_PER_POINT_STEP[precision]
+        if taylor:      # the depth phase also reads the second factor's multipliers
+            bpp += BYTES_PER_POINT_STEP[precision] // 5
         roof = None
         if kns and fp32:
             achieved = bpp * point_steps / (kns * 1e-9) / 1e9
-            kname = "k_march_persistent<float2>"
+            kname = ("k_phaseA_taylor<float2> + k_phaseB<float2> (per-step launches)" if taylor
+                     else "k_march_persistent<float2>")
             roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "peak_source": f"{peak_kind} hbm_gbs", "kernel": kname,
                     "algorithmic_bytes_per_launch": bpp * point_steps, "kernel_ms": kns / 1e6,
@@ -445,6 +462,8 @@ def run_ours(args):
                 "precision": "complex64 march, FP64 coefficient setup" if fp32 else "complex128",
                 "exec": ["auto", "stream", "graph", "persistent"][info["exec"]],
                 "fp64_residual_correction_every": args.rc or None,
+                "scheme": ("Taylor form of Eq. 3: [1 -+ (d/2)(X/2 - X^2/8)], two tridiagonal factors"
+                           if taylor else "Eq. 4 (Pade)"),
                 "medium": ("n^2 interpolated linearly in range between the slices; FP64 depth systems set up "
                            "for every range step" if interp else
                            "piecewise constant in range, FP64 depth systems set up per slice"),

@@ -92,6 +92,20 @@ extern "C" {
                                    slice and its slope (32 B per grid point per
                                    slice). */
 
+#define PE3D_OPT_SCHEME    10   /* one of PE3D_SCHEME_*; allowed only before
+                                   pe3d_set_medium                                */
+
+/* depth operator of the range step (pe3d_set_option PE3D_OPT_SCHEME) */
+#define PE3D_SCHEME_PADE   0    /* Eq. 4: [1 + (1/4 -+ d/4) X] (default)           */
+#define PE3D_SCHEME_TAYLOR 1    /* Eq. 3's Taylor form sqrt(1+x) ~ 1 + x/2 - x^2/8
+                                   under the same split: [1 -+ (d/2)(X/2 - X^2/8)],
+                                   X^2 the square of the discrete X.  Runs in the
+                                   stream and graph launches (PE3D_EXEC_AUTO picks
+                                   the stream launch); not with the persistent
+                                   launch, an interpolated medium, the FP64
+                                   correction or pe3d_march_batched.  Keeps the
+                                   depth multipliers of two factors per slice.   */
+
 /* stored quantity (pe3d_set_option PE3D_OPT_OUTPUT), Fig. 2 lines 10 and 13 */
 #define PE3D_OUT_FIELD     0    /* the envelope u (default)                          */
 #define PE3D_OUT_PRESSURE  1    /* p = u H0^(1)(k0 r), the Hankel factor of the split

@@ -46,6 +46,9 @@ PE3D_OPT_OUTPUT = 6
 PE3D_OPT_CTAS = 7
 PE3D_OPT_Y_MIDPOINT = 8
 PE3D_OPT_MEDIUM_INTERP = 9
+PE3D_OPT_SCHEME = 10
+PE3D_SCHEME_PADE = 0
+PE3D_SCHEME_TAYLOR = 1
 PE3D_OUT_FIELD = 0
 PE3D_OUT_PRESSURE = 1
 PE3D_OUT_TL = 2
@@ -333,7 +336,7 @@ class Plan:
 
     def __init__(self, Nz, Ntheta, dz, dtheta, dr, k0, *, periodic=False, fp32=False, stream=None,
                  exec_mode=None, zthreads=None, ttile=None, output=None, ctas=None, y_midpoint=None,
-                 interp=None):
+                 interp=None, scheme=None):
         import torch
         self.torch = torch
         if stream is None:
@@ -354,6 +357,8 @@ class Plan:
             pe3d_set_option(self.h, PE3D_OPT_CTAS, ctas)
         if y_midpoint is not None:
             pe3d_set_option(self.h, PE3D_OPT_Y_MIDPOINT, int(y_midpoint))
+        if scheme is not None:
+            pe3d_set_option(self.h, PE3D_OPT_SCHEME, int(scheme))
         if interp is not None:
             pe3d_set_option(self.h, PE3D_OPT_MEDIUM_INTERP, int(interp))
         self.output = PE3D_OUT_FIELD if output is None else output

@@ -244,8 +244,17 @@ int pe3d_set_option(pe3d_plan_t p, int option, int value) {
             if (value != 0 && value != 1) return fail(PE3D_ERR_ARG, "Y_MIDPOINT must be 0 or 1");
             p->y_mid = value;
             return PE3D_OK;
+        case PE3D_OPT_SCHEME:
+            if (value != PE3D_SCHEME_PADE && value != PE3D_SCHEME_TAYLOR) return fail(PE3D_ERR_ARG, "unknown scheme");
+            if (p->n2) return fail(PE3D_ERR_STATE, "SCHEME is allowed only before pe3d_set_medium");
+            if (value == PE3D_SCHEME_TAYLOR && (p->interp || p->rc_every > 0))
+                return fail(PE3D_ERR_ARG, "the Taylor form takes neither an interpolated medium nor the correction");
+            p->scheme = value;
+            return PE3D_OK;
         case PE3D_OPT_MEDIUM_INTERP: {
             if (value != 0 && value != 1) return fail(PE3D_ERR_ARG, "MEDIUM_INTERP must be 0 or 1");
+            if (value && p->scheme == PE3D_SCHEME_TAYLOR)
+                return fail(PE3D_ERR_ARG, "the Taylor form takes no interpolated medium");
             const int was = p->interp;
             p->interp = value;
             // per-slice multipliers, or slopes for interpolation, of the medium already set
@@ -255,6 +264,8 @@ int pe3d_set_option(pe3d_plan_t p, int option, int value) {
         case PE3D_OPT_RC_EVERY:
             if (value < 0) return fail(PE3D_ERR_ARG, "RC_EVERY must be >= 0");
             if (value > 0 && p->precision != PE3D_FP32) return fail(PE3D_ERR_ARG, "residual correction is for FP32 plans");
+            if (value > 0 && p->scheme == PE3D_SCHEME_TAYLOR)
+                return fail(PE3D_ERR_ARG, "the residual correction is for the Eq. 4 scheme");
             p->rc_every = value;
             return PE3D_OK;
         default:
@@ -275,6 +286,7 @@ int pe3d_get_option(pe3d_plan_t p, int option, int* value) {
         case PE3D_OPT_CTAS: *value = p->ctas_per_sm; return PE3D_OK;
         case PE3D_OPT_Y_MIDPOINT: *value = p->y_mid; return PE3D_OK;
         case PE3D_OPT_MEDIUM_INTERP: *value = p->interp; return PE3D_OK;
+        case PE3D_OPT_SCHEME: *value = p->scheme; return PE3D_OK;
         default: return fail(PE3D_ERR_ARG, "unknown option");
     }
 }
@@ -291,7 +303,7 @@ static int upload_medium(pe3d_plan_s* p, const void* n2, const double* slice_r, 
     int rc = fix_layout(p);
     if (rc) return rc;
     const size_t nb = (size_t)K * p->Nt * p->Nz * 16;
-    const size_t mb = (size_t)K * p->Nt * p->ldz * elem_bytes(p);
+    const size_t mb = (size_t)K * p->Nt * p->ldz * elem_bytes(p) * (p->scheme == PE3D_SCHEME_TAYLOR ? 2 : 1);
     p->medium_ready = false;
     if (nb != p->n2_bytes) {
         dev_free(p, &p->n2, p->n2_bytes);
@@ -336,11 +348,11 @@ int pe3d_set_medium_batched(int n, const pe3d_plan_t* plans, const void* const* 
     int rc;
     for (int i = 0; i < n; ++i)
         if ((rc = upload_medium(plans[i], n2[i], slice_r[i], K[i], n2_on_device))) return rc;
-    // one depth set-up launch for the piecewise media; interpolated ones get their slopes
+    // one depth set-up launch for the piecewise Eq. 4 media; the others set up on their own
     std::vector<pe3d_plan_s*> flat;
     for (int i = 0; i < n; ++i) {
         PE3D_CUDA(cudaMemsetAsync(plans[i]->status, 0, sizeof(int), plans[i]->stream));
-        if (plans[i]->interp) {
+        if (plans[i]->interp || plans[i]->scheme == PE3D_SCHEME_TAYLOR) {   // slopes, or two factors
             if ((rc = plans[i]->precision == PE3D_FP32 ? setupA_f32(plans[i]) : setupA_f64(plans[i]))) return rc;
         } else {
             flat.push_back(plans[i]);
@@ -426,6 +438,8 @@ int pe3d_march_batched(int n, const pe3d_plan_t* plans, const void* const* u0, c
         if (plans[i]->precision != prec) return fail(PE3D_ERR_ARG, "plans must share one precision");
         if (!plans[i]->medium_ready) return fail(PE3D_ERR_STATE, "every plan needs its medium");
         if (steps[i] < 0 || out_stride[i] < 1 || !(r0[i] > 0)) return fail(PE3D_ERR_ARG, "bad steps/stride/r0");
+        if (plans[i]->scheme == PE3D_SCHEME_TAYLOR)
+            return fail(PE3D_ERR_ARG, "batched marches take the Eq. 4 scheme");
     }
     int rc = prec == PE3D_FP32 ? batched_f32(n, plans, u0, r0, steps, out_stride, out)
                                : batched_f64(n, plans, u0, r0, steps, out_stride, out);
@@ -503,7 +517,7 @@ static int relayout(pe3d_plan_s* p, int T, int TZ) {
     p->ttile = TZ;
     int rc = fix_layout(p);
     if (rc) return rc;
-    const size_t mb = (size_t)p->nslices * p->Nt * p->ldz * elem_bytes(p);
+    const size_t mb = (size_t)p->nslices * p->Nt * p->ldz * elem_bytes(p) * (p->scheme == PE3D_SCHEME_TAYLOR ? 2 : 1);
     if ((rc = dev_alloc(p, &p->mz, mb))) return rc;
     p->mz_bytes = mb;
     if ((rc = slice_setup(p))) return rc;
@@ -531,7 +545,8 @@ int pe3d_autotune(pe3d_plan_t p, double r0, int steps) {
     int bestT = T0, bestTZ = TZ0, bestC = p->ctas_per_sm;
     const int Ts[4] = {32, 64, 128, 256}, TZs[5] = {2, 4, 8, 16, 32};
     // the persistent march also tries two CTAs per SM
-    const bool persistent = p->exec == PE3D_EXEC_AUTO || p->exec == PE3D_EXEC_PERSISTENT;
+    const bool persistent = (p->exec == PE3D_EXEC_AUTO || p->exec == PE3D_EXEC_PERSISTENT) &&
+                            p->scheme != PE3D_SCHEME_TAYLOR;
     const int ncand = persistent ? 2 : 1;
     for (int ti = 0; ti < 4 && !rc; ++ti) {
         for (int zi = 0; zi < 5 && !rc; ++zi) {

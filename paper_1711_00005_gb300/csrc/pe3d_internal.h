@@ -33,6 +33,7 @@ struct pe3d_plan_s {
     int out_mode = PE3D_OUT_FIELD;   // what the snapshots hold
     int y_mid = 0;                   // Y at the step's midpoint instead of r_{j+1}
     int interp = 0;                  // n^2 interpolated linearly in range, set up every step
+    int scheme = PE3D_SCHEME_PADE;   // depth operator: Eq. 4 or the Taylor form of Eq. 3
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // around the range-step kernels
     cudaEvent_t ev2 = nullptr, ev3 = nullptr;   // around the per-march set-up
     cudaStream_t capture = nullptr;   // private stream for graph capture

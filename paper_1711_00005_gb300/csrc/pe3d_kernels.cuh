@@ -85,6 +85,10 @@ struct MarchArgs {
     const C* zsm;               // [steps][NtP] Sherman-Morrison vector (periodic)
     const StepConst* sc;        // [steps]
     C c1, c2p;                  // v = c1 w + c2p * (scaled depth solution)
+    // Taylor form of Eq. 3: the depth factor is (I + a1 X)(I + a2 X); v = c1 w +
+    // c21 * (scaled solution with factor 1) + c22 * (scaled solution with factor 2)
+    const C* mz2 = nullptr;     // [slices][Nt][ldz] multipliers of factor 2 (mz: factor 1)
+    C c21, c22;
     C* snap;                    // [n_out][Nt][snap_ld] or nullptr (real for OUT_TL)
     int snap_ld;
     int out_mode = OUT_FIELD;   // what the snapshots hold (OUT_*)
@@ -315,6 +319,122 @@ __device__ bool computeA(const MarchArgs<C>& P, int base, unsigned char* smem, i
     }
     __syncthreads();
     PE3D_MARK(7);
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// phase A of the Taylor form of Eq. 3.  Its depth factor
+// I - (d/4) X + (d/16) X^2 is pentadiagonal, but as a quadratic in X it is the
+// product (I + a1 X)(I + a2 X) of two tridiagonal factors (a1, a2 the roots of
+// a^2 + (d/4) a + d/16), and by partial fractions
+//   (I + a1 X)^-1 (I + a2 X)^-1 = g1 (I + a1 X)^-1 + g2 (I + a2 X)^-1,
+// g1 = a1 / (a1 - a2), g2 = -a2 / (a1 - a2).  So a unit solves both factors
+// from the same w in shared memory and adds the scaled solutions:
+// v = 2 A^-1 w - w = c1 w + c21 y1 + c22 y2.
+// ---------------------------------------------------------------------------
+
+template <typename C>
+__host__ __device__ inline size_t grpA3_bytes(int ldz) { return align128((size_t)3 * ldz * sizeof(C)); }
+
+// thread 0: the unit's columns of w and of both factors' multipliers
+template <typename C>
+__device__ __forceinline__ void loadA_taylor(const MarchArgs<C>& P, int slice, int base, unsigned char* smem,
+                                             uint32_t& par) {
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem) + MB_A;
+    par |= 1u << (INFLIGHT + MB_A);
+    const int ldz = P.ldz;
+    const size_t gstride = grpA3_bytes<C>(ldz);
+    const C* m1 = P.mz + (long long)slice * P.slice_stride;
+    const C* m2 = P.mz2 + (long long)slice * P.slice_stride;
+    const int nact = min(P.NG, P.Nt - base);
+    const uint32_t colb = (uint32_t)(ldz * sizeof(C));
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(mbar, 3u * nact * colb);
+    for (int g = 0; g < nact; ++g) {
+        C* dw = reinterpret_cast<C*>(smem + P.sp.a[0] + g * gstride);
+        bulk_g2s(dw, P.w + (size_t)(base + g) * ldz, colb, mbar);
+        bulk_g2s(dw + ldz, m1 + (size_t)(base + g) * ldz, colb, mbar);
+        bulk_g2s(dw + 2 * ldz, m2 + (size_t)(base + g) * ldz, colb, mbar);
+    }
+}
+
+// Solve both factors of the unit from w, form v and store its columns
+template <typename C, int LA>
+__device__ bool computeA_taylor(const MarchArgs<C>& P, int base, unsigned char* smem, uint32_t& par) {
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem) + MB_A;
+    const int tid = threadIdx.x;
+    const int gs = tid / P.T, k = tid - gs * P.T;
+    const int ldz = P.ldz, L = P.L;
+    const size_t gstride = grpA3_bytes<C>(ldz);
+    C* sw = reinterpret_cast<C*>(smem + P.sp.a[0] + gs * gstride);
+    Aff<C>* scr = reinterpret_cast<Aff<C>*>(smem + P.sp.scrA) + gs * 16;
+
+    const bool ok = mbar_wait_bounded(mbar, (par >> MB_A) & 1u, P.status, ST_TIMEOUT);
+    par ^= 1u << MB_A;
+    par &= ~(1u << (INFLIGHT + MB_A));
+    if (!__syncthreads_and(ok)) return false;
+
+    ScanGeom geo;
+    geo.S = 1; geo.KW = 32; geo.kw = k & 31; geo.W = P.T >> 5; geo.wk = k >> 5; geo.sstride = 1;
+    C* wk_ = sw + k * L;
+    const C one = cone<C>(), zero = czero<C>();
+    // elements i >= L act as the identity map (mu = 1, w = 0)
+    auto W_ = [&](int i) -> C {
+        const int ii = min(i, L - 1);
+        return i < L ? wk_[ii] : zero;
+    };
+    C acc[LA], gq[LA];
+#pragma unroll
+    for (int i = 0; i < LA; ++i) acc[i] = cmul(P.c1, W_(i));
+#pragma unroll 1
+    for (int f = 0; f < 2; ++f) {
+        const C* mk = sw + (1 + f) * ldz + k * L;
+        const C cf = f == 0 ? P.c21 : P.c22;
+        auto M_ = [&](int i) -> C {
+            const int ii = min(i, L - 1);
+            return i < L ? mk[ii] : one;
+        };
+        Aff<C> agg; agg.a = one; agg.b = zero;          // forward elimination
+#pragma unroll
+        for (int i = 0; i < LA; ++i) {
+            agg.b = cfma(M_(i), agg.b, cmul(M_(i), W_(i)));
+            agg.a = cmul(M_(i), agg.a);
+        }
+        C g = scan_carry<C, true>(agg, geo, scr);
+#pragma unroll
+        for (int i = 0; i < LA; ++i) {
+            g = cfma(M_(i), g, cmul(M_(i), W_(i)));
+            gq[i] = i < L ? g : zero;
+        }
+        agg.a = one; agg.b = zero;                      // back substitution
+#pragma unroll
+        for (int i = LA - 1; i >= 0; --i) {
+            agg.b = cfma(M_(i), agg.b, gq[i]);
+            agg.a = cmul(M_(i), agg.a);
+        }
+        C y = scan_carry<C, false>(agg, geo, scr);
+#pragma unroll
+        for (int i = LA - 1; i >= 0; --i) {
+            y = cfma(M_(i), y, gq[i]);
+            acc[i] = cfma(cf, y, acc[i]);
+        }
+    }
+    __syncthreads();                                    // both solves have read w
+#pragma unroll
+    for (int i = 0; i < LA; ++i)
+        if (i < L) wk_[i] = acc[i];                     // v over w
+    __syncthreads();
+    {
+        const int nact = min(P.NG, P.Nt - base);
+        const int n16 = (int)(ldz * sizeof(C) / 16);
+        const float4* s4 = reinterpret_cast<const float4*>(smem + P.sp.a[0]);
+        const int g16 = (int)(gstride / 16);
+        for (int i = tid; i < nact * n16; i += NT) {
+            const int gg = i / n16, e = i - gg * n16;
+            __stcg(reinterpret_cast<float4*>(P.v + (size_t)(base + gg) * ldz) + e, s4[gg * g16 + e]);
+        }
+    }
+    __syncthreads();
     return true;
 }
 
@@ -583,6 +703,17 @@ __global__ void __launch_bounds__(NT) k_phaseA(const __grid_constant__ MarchArgs
     const int base = blockIdx.x * P.NG;
     if (threadIdx.x == 0) loadA(P, P.slice_of_step[j], base, smem, 0, true, par);
     if (!computeA<C, LA>(P, base, smem, 0, par)) drain_copies(smem, par);
+}
+
+// the depth phase of the Taylor form (stream and graph launches)
+template <typename C, int LA>
+__global__ void __launch_bounds__(NT) k_phaseA_taylor(const __grid_constant__ MarchArgs<C> P, int j) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    init_mbarriers(smem);
+    uint32_t par = 0;
+    const int base = blockIdx.x * P.NG;
+    if (threadIdx.x == 0) loadA_taylor(P, P.slice_of_step[j], base, smem, par);
+    if (!computeA_taylor<C, LA>(P, base, smem, par)) drain_copies(smem, par);
 }
 
 template <typename C, int LB>

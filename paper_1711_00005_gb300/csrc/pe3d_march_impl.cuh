@@ -109,6 +109,41 @@ inline DepthConsts depth_consts(const pe3d_plan_s* p) {
     return c;
 }
 
+// The Taylor form of Eq. 3: I - (d/4) X + (d/16) X^2 = (I + a1 X)(I + a2 X)
+// with a1, a2 the roots of a^2 + (d/4) a + d/16; e_k = a_k s is factor k's
+// off-diagonal.  v = 2 A^-1 w - w with A^-1 = g1 (I + a1 X)^-1 + g2 (I + a2 X)^-1
+// (g1 = a1 / (a1 - a2), g2 = -a2 / (a1 - a2)); the kernels carry factor k's
+// solution scaled by -e_k, so v = -w + c2[0] y1 + c2[1] y2 with
+// c2[k] = -2 g_k / e_k.
+struct TaylorConsts {
+    double2 a[2], einv[2], c2[2];
+};
+inline double2 h_sqrt(double2 z) {          // principal square root
+    const double r = std::hypot(z.x, z.y);
+    const double re = std::sqrt(0.5 * (r + z.x));
+    const double im = std::copysign(std::sqrt(0.5 * (r - z.x)), z.y);
+    return d2(re, im);
+}
+inline TaylorConsts taylor_consts(const pe3d_plan_s* p) {
+    const double2 d = d2(0.0, p->k0 * p->dr);
+    const double s = 1.0 / ((p->k0 * p->dz) * (p->k0 * p->dz));
+    // a = (-(d/4) +- sqrt(d^2/16 - d/4)) / 2
+    const double2 d4 = d2(d.x / 4.0, d.y / 4.0);
+    const double2 disc = d2(d4.x * d4.x - d4.y * d4.y - d4.x, 2.0 * d4.x * d4.y - d4.y);
+    const double2 sq = h_sqrt(disc);
+    TaylorConsts t;
+    t.a[0] = d2((-d4.x + sq.x) / 2.0, (-d4.y + sq.y) / 2.0);
+    t.a[1] = d2((-d4.x - sq.x) / 2.0, (-d4.y - sq.y) / 2.0);
+    const double2 diff = d2(t.a[0].x - t.a[1].x, t.a[0].y - t.a[1].y);
+    const double2 g[2] = {h_div(t.a[0], diff), h_div(d2(-t.a[1].x, -t.a[1].y), diff)};
+    for (int k = 0; k < 2; ++k) {
+        const double2 e = d2(t.a[k].x * s, t.a[k].y * s);
+        t.einv[k] = h_div(d2(1.0, 0.0), e);
+        t.c2[k] = h_div(d2(-2.0 * g[k].x, -2.0 * g[k].y), e);
+    }
+    return t;
+}
+
 // Depth systems of every slice, or, for an interpolated medium, each slice's
 // d/e and its change to the next slice (the per-step systems are then built
 // in the march)
@@ -136,6 +171,19 @@ int setupA(pe3d_plan_s* p) {
         return PE3D_OK;
     }
     const int KNt = p->nslices * p->Nt;
+    if (p->scheme == PE3D_SCHEME_TAYLOR) {
+        // the two tridiagonal factors I + a_k X of the Taylor form, slices of
+        // factor 1 then of factor 2
+        const TaylorConsts tc = taylor_consts(p);
+        for (int f = 0; f < 2; ++f) {
+            k_setupA<C><<<(KNt + 127) / 128, 128, 0, p->stream>>>(
+                reinterpret_cast<const double2*>(p->n2), KNt, p->Nz, p->ldz, tc.a[f], s, tc.einv[f],
+                reinterpret_cast<C*>(p->mz) + (size_t)f * KNt * p->ldz, p->status);
+            PE3D_CUDA(cudaGetLastError());
+        }
+        p->total_launches += 2;
+        return PE3D_OK;
+    }
     k_setupA<C><<<(KNt + 127) / 128, 128, 0, p->stream>>>(
         reinterpret_cast<const double2*>(p->n2), KNt, p->Nz, p->ldz, alpha, s, einv,
         reinterpret_cast<C*>(p->mz), p->status);
@@ -171,6 +219,14 @@ void fill_args(pe3d_plan_s* p, MarchArgs<C>& A) {
     const double2 c2p = h_div(d2(-(1.0 - c1.x), c1.y), e);
     A.c1 = from64<C>(c1);
     A.c2p = from64<C>(c2p);
+    A.mz2 = nullptr;
+    if (p->scheme == PE3D_SCHEME_TAYLOR) {
+        const TaylorConsts tc = taylor_consts(p);
+        A.c1 = from64<C>(d2(-1.0, 0.0));
+        A.c21 = from64<C>(tc.c2[0]);
+        A.c22 = from64<C>(tc.c2[1]);
+        A.mz2 = A.mz + (size_t)p->nslices * p->Nt * p->ldz;
+    }
     A.snap = nullptr; A.snap_ld = p->Nz; A.stride = 1;
     A.out_mode = p->out_mode;
     A.y_mid = p->y_mid;
@@ -188,9 +244,12 @@ void fill_args(pe3d_plan_s* p, MarchArgs<C>& A) {
 template <typename C>
 struct KernelTable {
     const void* A[4];
+    const void* A_taylor[4];
     const void* B[4];
     const void* persist[4][4];
     KernelTable() {
+        A_taylor[0] = (const void*)k_phaseA_taylor<C, 5>;  A_taylor[1] = (const void*)k_phaseA_taylor<C, 9>;
+        A_taylor[2] = (const void*)k_phaseA_taylor<C, 17>; A_taylor[3] = (const void*)k_phaseA_taylor<C, 33>;
         A[0] = (const void*)k_phaseA<C, 5>;  A[1] = (const void*)k_phaseA<C, 9>;
         A[2] = (const void*)k_phaseA<C, 17>; A[3] = (const void*)k_phaseA<C, 33>;
         B[0] = (const void*)k_phaseB<C, 5>;  B[1] = (const void*)k_phaseB<C, 9>;
@@ -214,6 +273,13 @@ const KernelTable<C>& kernels() {
 template <typename C>
 SmemPlan single_unit_plan(const pe3d_plan_s* p) {
     SmemPlan sp{};
+    if (p->scheme == PE3D_SCHEME_TAYLOR) {   // w and both factors' multipliers per system
+        if (!plan_smem_sizes<C>((size_t)p->NG * grpA3_bytes<C>(p->ldz), tile_bytes<C>(p->rowsB, p->TZ),
+                                coef_bytes<C>(p->NtP, p->boundary == PE3D_PERIODIC), p->NG, p->TZ, false, false,
+                                false, true, SMEM_BUDGET, &sp))
+            sp.total = 0;                    // does not fit: run_steps refuses the march
+        return sp;
+    }
     plan_smem<C>(p->NG, p->ldz, p->rowsB, p->TZ, p->NtP, p->boundary == PE3D_PERIODIC, false, false, false, true,
                  SMEM_BUDGET, &sp);   // layout_choose guarantees it fits
     return sp;
@@ -258,6 +324,9 @@ int prepare_kernels(const pe3d_plan_s* p) {
         for (int a = 0; a < 4; ++a) {
             PE3D_CUDA(cudaFuncSetAttribute(t.A[a], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BUDGET));
             PE3D_CUDA(cudaFuncSetAttribute(t.A[a], cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+            PE3D_CUDA(cudaFuncSetAttribute(t.A_taylor[a], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)SMEM_BUDGET));
+            PE3D_CUDA(cudaFuncSetAttribute(t.A_taylor[a], cudaFuncAttributePreferredSharedMemoryCarveout, 100));
             PE3D_CUDA(cudaFuncSetAttribute(t.B[a], cudaFuncAttributePreferredSharedMemoryCarveout, 100));
             PE3D_CUDA(cudaFuncSetAttribute(t.B[a], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BUDGET));
             for (int b = 0; b < 4; ++b)
@@ -405,8 +474,11 @@ int launch_prologue(pe3d_plan_s* p, const void* u0_dev, double r0) {
 
 template <typename C>
 int run_steps(pe3d_plan_s* p, MarchArgs<C>& A, int steps) {
+    const bool taylor = p->scheme == PE3D_SCHEME_TAYLOR;
     int exec = p->exec;
-    if (exec == PE3D_EXEC_AUTO) exec = PE3D_EXEC_PERSISTENT;
+    if (exec == PE3D_EXEC_AUTO) exec = taylor ? PE3D_EXEC_STREAM : PE3D_EXEC_PERSISTENT;
+    if (taylor && exec == PE3D_EXEC_PERSISTENT)
+        return fail(PE3D_ERR_ARG, "the Taylor form runs in the stream and graph launches");
     p->last_exec = exec;
     const int unitsA = (p->Nt + p->NG - 1) / p->NG;
     const KernelTable<C>& kt = kernels<C>();
@@ -437,9 +509,14 @@ int run_steps(pe3d_plan_s* p, MarchArgs<C>& A, int steps) {
     }
     cudaError_t e = cudaSuccess;
     A.sp = single_unit_plan<C>(p);
+    if (A.sp.total == 0) {
+        if (exec == PE3D_EXEC_GRAPH) { cudaGraph_t g = nullptr; cudaStreamEndCapture(ls, &g); if (g) cudaGraphDestroy(g); }
+        return fail(PE3D_ERR_ARG, "the Taylor form's depth unit does not fit in shared memory for this layout");
+    }
+    const void* kA = taylor ? kt.A_taylor[ca] : kt.A[ca];
     for (int j = 0; j < steps && e == cudaSuccess; ++j) {
         void* args[] = {&A, &j};
-        e = cudaLaunchKernel(kt.A[ca], dim3(unitsA), dim3(NT), args, A.sp.total, ls);
+        e = cudaLaunchKernel(kA, dim3(unitsA), dim3(NT), args, A.sp.total, ls);
         if (e == cudaSuccess) e = cudaLaunchKernel(kt.B[cb], dim3(p->tiles), dim3(NT), args, A.sp.total, ls);
     }
     if (exec == PE3D_EXEC_GRAPH) {
