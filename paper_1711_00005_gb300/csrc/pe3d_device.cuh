@@ -270,6 +270,11 @@ struct MediumStep {
     int k, k1;
     double t;
 };
+// d/e of one depth row of a slice and its change to the next slice
+// (interpolated medium): d/e at t between slices k and k+1 is d + t dd
+struct alignas(32) DiagSlope {
+    double2 d, dd;
+};
 __host__ __device__ __forceinline__ double2 medium_lerp(double2 a, double2 b, double t) {
     const double u = 1.0 - t;
     return make_double2(fma(t, b.x, u * a.x), fma(t, b.y, u * a.y));

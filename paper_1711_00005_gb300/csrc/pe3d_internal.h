@@ -61,7 +61,7 @@ struct pe3d_plan_s {
     size_t mz_bytes = 0;
     void* mzs = nullptr;              // [steps][Nt][ldz] per-step multipliers (interpolated medium)
     size_t mzs_bytes = 0;
-    void* dd = nullptr;               // double4 [nslices][Nt][Nz]: d/e and its change (interpolated medium)
+    void* dd = nullptr;               // DiagSlope [nslices][Nt][Nz]: d/e and its change (interpolated medium)
     size_t dd_bytes = 0;
     // per-step arrays
     void* mB = nullptr;               // [steps][NtP]

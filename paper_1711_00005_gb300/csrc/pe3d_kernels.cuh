@@ -1211,7 +1211,7 @@ __global__ void k_setupA_multi(const SetupADesc<C>* __restrict__ d, const int* _
 // is D_k + t (D_{k+1} - D_k).
 template <typename C>
 __global__ void k_setupA_slopes(const double2* __restrict__ n2, int K, long long pts, double2 alpha, double s,
-                                double2 einv, double4* __restrict__ dd) {
+                                double2 einv, DiagSlope* __restrict__ dd) {
     const DiagOverE doe(alpha, s, einv);
     const long long n = (long long)K * pts;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -1221,7 +1221,7 @@ __global__ void k_setupA_slopes(const double2* __restrict__ n2, int K, long long
             const double2 d1 = doe(n2[i + pts]);
             dd1 = make_double2(d1.x - d0.x, d1.y - d0.y);
         }
-        dd[i] = make_double4(d0.x, d0.y, dd1.x, dd1.y);
+        dd[i] = DiagSlope{d0, dd1};
     }
 }
 
@@ -1230,19 +1230,19 @@ __global__ void k_setupA_slopes(const double2* __restrict__ n2, int K, long long
 // k_setupA_slopes and lerp[j] = (k, k1, t): d / e = D_k + t (D_k1 - D_k).
 // Step j's multipliers go to slot j % ring of mz.
 template <typename C>
-__global__ void k_setupA_lerp(const double4* __restrict__ dd, const MediumStep* __restrict__ lerp, int j_first,
+__global__ void k_setupA_lerp(const DiagSlope* __restrict__ dd, const MediumStep* __restrict__ lerp, int j_first,
                               int count, int ring, int Nt, int Nz, int ldz, C* __restrict__ mz, int* status) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= count * Nt) return;
     const int jj = idx / Nt, m = idx - jj * Nt;
     const int j = j_first + jj;
     const MediumStep ms = lerp[j];
-    const double4* row = dd + ((size_t)ms.k * Nt + m) * Nz;
+    const DiagSlope* row = dd + ((size_t)ms.k * Nt + m) * Nz;
     const double t = ms.t;
     C* out = mz + ((size_t)(j % ring) * Nt + m) * ldz;
     if (!depth_pivots<C>([row, t](int l) {
-            const double4 q = row[l];
-            return make_double2(fma(t, q.z, q.x), fma(t, q.w, q.y));
+            const DiagSlope q = row[l];
+            return make_double2(fma(t, q.dd.x, q.d.x), fma(t, q.dd.y, q.d.y));
         }, Nz, ldz, out))
         atomicExch(status, ST_SINGULAR);
 }

@@ -154,7 +154,7 @@ int setupA(pe3d_plan_s* p) {
     const double s = dc.s;
     if (p->interp) {
         const long long pts = (long long)p->Nt * p->Nz;
-        const size_t b = (size_t)p->nslices * pts * sizeof(double4);
+        const size_t b = (size_t)p->nslices * pts * sizeof(DiagSlope);
         if (b != p->dd_bytes) {
             dev_free(p, &p->dd, p->dd_bytes);
             p->dd_bytes = 0;
@@ -165,7 +165,7 @@ int setupA(pe3d_plan_s* p) {
         const long long n = (long long)p->nslices * pts;
         const int grid = (int)std::min<long long>((n + 255) / 256, 16LL * p->num_sms);
         k_setupA_slopes<C><<<grid, 256, 0, p->stream>>>(reinterpret_cast<const double2*>(p->n2), p->nslices, pts,
-                                                        alpha, s, einv, reinterpret_cast<double4*>(p->dd));
+                                                        alpha, s, einv, reinterpret_cast<DiagSlope*>(p->dd));
         PE3D_CUDA(cudaGetLastError());
         p->total_launches += 1;
         return PE3D_OK;
@@ -350,7 +350,7 @@ int interp_setup(pe3d_plan_s* p, int j_first, int count, int ring, cudaStream_t 
     if (n <= 0) return PE3D_OK;
     if (n > INT_MAX) return fail(PE3D_ERR_ARG, "steps x Ntheta too large for an interpolated medium");
     k_setupA_lerp<C><<<(int)((n + 127) / 128), 128, 0, st>>>(
-        reinterpret_cast<const double4*>(p->dd), reinterpret_cast<const MediumStep*>(p->lerp), j_first, count,
+        reinterpret_cast<const DiagSlope*>(p->dd), reinterpret_cast<const MediumStep*>(p->lerp), j_first, count,
         ring, p->Nt, p->Nz, p->ldz, reinterpret_cast<C*>(p->mzs), p->status);
     PE3D_CUDA(cudaGetLastError());
     return PE3D_OK;
