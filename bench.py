@@ -233,6 +233,12 @@ def run_reference(args):
         if rank != 0:
             barrier()
             return 0
+    if args.workload not in WORKLOADS:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm covers the single-march workloads; "
+                          f"{args.workload} reports its oracle sample as cpu_baseline in its own line"}), flush=True)
+        if world > 1:
+            barrier()
+        return 0
     import oracle
     precision, make = WORKLOADS[args.workload]
     wl = make()
