@@ -86,7 +86,7 @@ extern "C" {
                                    (held at the first/last slice outside their
                                    span), with the depth systems set up in FP64 for
                                    every range step of a march before it runs
-                                   (Fig. 2 line 7 run per step): Nt*ldz complex of
+                                   (Fig. 2's update of A run per step): Nt*ldz complex of
                                    the plan precision per step of the longest
                                    march.  pe3d_set_medium then keeps d/e of each
                                    slice and its slope (32 B per grid point per
@@ -106,12 +106,12 @@ extern "C" {
                                    correction or pe3d_march_batched.  Keeps the
                                    depth multipliers of two factors per slice.   */
 
-/* stored quantity (pe3d_set_option PE3D_OPT_OUTPUT), Fig. 2 lines 10 and 13 */
+/* stored quantity (pe3d_set_option PE3D_OPT_OUTPUT), Sec. 2 and Fig. 2      */
 #define PE3D_OUT_FIELD     0    /* the envelope u (default)                          */
 #define PE3D_OUT_PRESSURE  1    /* p = u H0^(1)(k0 r), the Hankel factor of the split
-                                   p = u w(r) (Sec. 2, Fig. 2 line 10); complex      */
-#define PE3D_OUT_TL        2    /* transmission loss -20 log10 |p| in dB (Fig. 2
-                                   line 13, Fig. 5); real                            */
+                                   p = u w(r) (Sec. 2, Fig. 2); complex             */
+#define PE3D_OUT_TL        2    /* transmission loss -20 log10 |p| in dB (Fig. 2,
+                                   Fig. 5); real                                     */
 
 typedef struct pe3d_plan_s *pe3d_plan_t;
 
@@ -135,7 +135,7 @@ int pe3d_set_option(pe3d_plan_t plan, int option, int value);
 int pe3d_get_option(pe3d_plan_t plan, int option, int *value);
 
 /* Upload the medium and build the depth-system coefficients (Eq. 7's A for
- * every slice, FP64; "update matrix A" of Fig. 2).
+ * every slice, FP64; the update of A in Fig. 2).
  *   n2        complex128 [K][Ntheta][Nz], n^2 = (c0/c)^2 + i * absorption,
  *             host or device memory (n2_on_device)
  *   slice_r   host double [K], ascending ranges: slice k is active for
@@ -149,7 +149,7 @@ int pe3d_set_medium(pe3d_plan_t plan, const void *n2, const double *slice_r, int
                     int n2_on_device);
 
 /* March `steps` range steps from the field u0 at range r0 (the loop of
- * Fig. 2, lines 4-11; operators at r* = r0 + (j+1) dr for step j).
+ * the range loop of Fig. 2; operators at r* = r0 + (j+1) dr for step j).
  *   u0        [Ntheta][Nz] complex (plan precision), host or device
  *   r0        starting range [m] (> 0; Y carries 1/r^2)
  *   steps     number of range steps (>= 0)
@@ -199,7 +199,7 @@ int pe3d_autotune(pe3d_plan_t plan, double r0, int steps);
 
 /* Batched multi-march: advance n independent plans (unequal Nz, Ntheta
  * allowed; same precision and stream) in shared launches, the paper's
- * frequency loop (Fig. 2 lines 1 and 12; Sec. 3.2.3) on one GPU.  Per plan i
+ * frequency loop (Fig. 2; Sec. 3.2.3) on one GPU.  Per plan i
  * the arguments mean what they mean in pe3d_march; all pointers are device
  * memory.  One cooperative launch advances up to 64 plans; a larger n runs
  * as consecutive launches of up to 64 on the plans' stream.

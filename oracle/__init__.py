@@ -150,7 +150,7 @@ def march_workload(wl, **kw):
 
 # ---------------------------------------------------------------------------
 # pressure and transmission loss (Sec. 2: p = u w(r) with w the Hankel
-# function H0^(1)(k0 r); Fig. 2 line 10 forms p every step, line 13 writes TL)
+# function H0^(1)(k0 r); Fig. 2 forms p every step and writes TL)
 # ---------------------------------------------------------------------------
 
 def hankel0(x):
@@ -175,7 +175,7 @@ def pressure(u_snaps, ranges, k0):
 
 
 def transmission_loss(p):
-    """TL = -20 log10 |p| in dB (Fig. 2 line 13, Fig. 5)."""
+    """TL = -20 log10 |p| in dB (Fig. 2, Fig. 5)."""
     return -20.0 * np.log10(np.abs(p))
 
 

@@ -193,7 +193,7 @@ int pe3d_plan(int Nz, int Ntheta, double dz, double dtheta, double dr, double k0
     return PE3D_OK;
 }
 
-// FP64 depth multipliers of every slice (Fig. 2 line 7).  An interpolated
+// FP64 depth multipliers of every slice (Fig. 2's update of A).  An interpolated
 // medium gets each slice's d/e and its slope instead, and its systems are set
 // up per range step in the march.
 static int slice_setup(pe3d_plan_s* p) {

@@ -260,7 +260,7 @@ struct StepConst {
     float2 nbinv32;  // nbinv and qnext rounded once to complex64 (the FP32 march
     float2 qnext32;  // reads these instead of converting per thread)
     double2 hk;      // H0^(1)(k0 r*) = J0 + i Y0 at this step's range: p = u hk
-    float2 hk32;     // (Fig. 2 line 10), and its complex64 copy
+    float2 hk32;     // (Sec. 2, Fig. 2), and its complex64 copy
     float2 pad_;
 };
 // Medium of one range step when n^2 is interpolated linearly in range:

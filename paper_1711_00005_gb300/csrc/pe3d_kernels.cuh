@@ -1090,7 +1090,7 @@ __global__ void k_prologue(const C* __restrict__ u0, int Nz, int Nt, int ldz, in
 }
 
 // ---------------------------------------------------------------------------
-// FP64 coefficient setup ("update matrix A and B", Fig. 2 line 7)
+// FP64 coefficient setup (the update of matrices A and B in Fig. 2)
 // ---------------------------------------------------------------------------
 
 // 1/x for 2^-53 <= x < 2^996: the hardware estimate (rcp.approx.ftz.f64)

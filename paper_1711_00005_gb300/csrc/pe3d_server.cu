@@ -1,5 +1,5 @@
 // pe3d_server.cu -- the request loop: continuous batching of independent
-// marches (the paper's multi-frequency farm, Fig. 2 lines 1 and 12, Sec.
+// marches (the paper's multi-frequency farm, Fig. 2's frequency loop, Sec.
 // 3.2.3) on one GPU.
 //
 // A scheduler thread owns one CUDA stream.  Each turn of its loop it

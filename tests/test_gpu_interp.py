@@ -1,6 +1,6 @@
 """Range-dependent medium refreshed every step: n^2 interpolated linearly in
 range between the slices around r* and the depth systems set up in FP64 for
-every range step (Fig. 2 line 7 run per step), against the oracle's
+every range step (Fig. 2's update of A, run per step), against the oracle's
 interpolating march (pinned in tests/pins.py:check_interp_linear).
 
 Tolerances as in test_gpu_parity.py: 1e-10 for the FP64 march, 2e-5 for

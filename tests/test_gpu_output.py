@@ -1,8 +1,8 @@
 """Pressure and transmission-loss snapshots (PE3D_OPT_OUTPUT) against the
 oracle (needs a GB300).
 
-The library forms p = u H0^(1)(k0 r) (Sec. 2; Fig. 2 line 10), with H0^(1)
-evaluated in FP64 per range step, and TL = -20 log10 |p| (Fig. 2 line 13) in
+The library forms p = u H0^(1)(k0 r) (Sec. 2; Fig. 2), with H0^(1)
+evaluated in FP64 per range step, and TL = -20 log10 |p| (Fig. 2) in
 the snapshot stores.  The oracle applies the same definitions to its own FP64
 march (scipy's hankel1, pinned in test_oracle_output.py).
 

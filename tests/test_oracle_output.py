@@ -1,8 +1,8 @@
 """Pins of the oracle's pressure and transmission-loss output (CPU).
 
 The paper recovers the pressure from the marched envelope as p = u w(r), with
-w the Hankel function H0^(1)(k0 r) (Sec. 2; Fig. 2 line 10), and writes the
-transmission loss -20 log10 |p| (Fig. 2 line 13; Fig. 5).  The oracle calls
+w the Hankel function H0^(1)(k0 r) (Sec. 2; Fig. 2), and writes the
+transmission loss -20 log10 |p| (Fig. 2; Fig. 5).  The oracle calls
 scipy's hankel1 for H0^(1); these tests fix that call to things other than
 itself:
   * Hankel's large-argument expansion of H0^(1) (DLMF 10.17.5), written out
