@@ -104,7 +104,10 @@ extern "C" {
                                    the stream launch); not with the persistent
                                    launch, an interpolated medium, the FP64
                                    correction or pe3d_march_batched.  Keeps the
-                                   depth multipliers of two factors per slice.   */
+                                   depth multipliers of two factors per slice; a
+                                   depth unit stages three columns per system, and
+                                   pe3d_march refuses (PE3D_ERR_ARG) a layout whose
+                                   unit does not fit in shared memory.           */
 
 /* stored quantity (pe3d_set_option PE3D_OPT_OUTPUT), Sec. 2 and Fig. 2      */
 #define PE3D_OUT_FIELD     0    /* the envelope u (default)                          */
@@ -129,8 +132,10 @@ typedef struct pe3d_plan_s *pe3d_plan_t;
 int pe3d_plan(int Nz, int Ntheta, double dz, double dtheta, double dr, double k0,
               int boundary, int precision, void *cuda_stream, pe3d_plan_t *out);
 
-/* Set an option (PE3D_OPT_*).  Layout options (ZTHREADS, TTILE) are allowed
- * only before pe3d_set_medium.  Errors: PE3D_ERR_ARG, PE3D_ERR_STATE. */
+/* Set an option (PE3D_OPT_*).  Layout options (ZTHREADS, TTILE) and SCHEME
+ * are allowed only before pe3d_set_medium.  Errors: PE3D_ERR_ARG (unknown
+ * option or value, or a combination the header rules out),
+ * PE3D_ERR_STATE. */
 int pe3d_set_option(pe3d_plan_t plan, int option, int value);
 int pe3d_get_option(pe3d_plan_t plan, int option, int *value);
 
