@@ -59,3 +59,19 @@ def test_reference_arm_under_torchrun():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_reference_arm_scope():
+    """The oracle arm times the single-march workloads (the Taylor form too)
+    and prints an unavailable line for the multi-march ones."""
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "broadband-120f",
+                        "--steps", "1", "--warmup", "3"], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][-1])
+    assert d["impl"] == "reference" and "unavailable" in d
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "medium-100Hz-taylor",
+                        "--steps", "1", "--warmup", "3", "--ref-sample-steps", "2"], cwd=ROOT, capture_output=True,
+                       text=True, timeout=600, env={**os.environ, "OMP_NUM_THREADS": "4"})
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][-1])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["config"]["workload"].endswith("-taylor")
