@@ -227,8 +227,10 @@ int pe3d_march_batched(int n, const pe3d_plan_t *plans, const void *const *u0, c
  *   A march whose scratch (fields, coefficients of all K slices, per-step
  *   tables) exceeds PE3D_STATIC_SCRATCH_BYTES is rejected with PE3D_ERR_ARG and
  *   a message giving the size it needs.
- *   The first call on a device looks up the array's device address (module
- *   load) and caches it: make that first call before any CUDA graph capture.
+ *   Every call looks up the array's device address in the current device's
+ *   context (cudaGetSymbolAddress, with that device current); the first call
+ *   on a device also loads the library's device code there, so make that
+ *   first call before any stream capture begins.
  *   Every call reuses the same array and leaves its contents behind; each call
  *   clears what must start at zero.  Calls that overlap on the GPU (two host
  *   threads, or two streams) race on the array: serialise them.  The call

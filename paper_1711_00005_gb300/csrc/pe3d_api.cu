@@ -4,8 +4,11 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <set>
 #include <string>
+#include <utility>
 
 #include "pe3d_internal.h"
 #include "pe3d_device.cuh"
@@ -89,6 +92,44 @@ int active_slice(const std::vector<double>& slice_r, double r) {
     for (size_t i = 0; i < slice_r.size(); ++i)
         if (slice_r[i] <= r) k = (int)i;
     return k;
+}
+
+// the calling thread's current CUcontext, through the runtime's driver entry
+// point (the library links no driver library); nullptr if unavailable
+static void* current_context() {
+    using GetFn = CUresult (*)(CUcontext*);
+    static GetFn get = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get = reinterpret_cast<GetFn>(fn);
+        else
+            cudaGetLastError();
+    });
+    CUcontext c = nullptr;
+    if (get && get(&c) != CUDA_SUCCESS) c = nullptr;
+    return c;
+}
+
+static std::mutex g_prep_mu;
+static std::set<std::pair<const void*, void*>> g_prepared;
+
+bool context_prepared(const void* table) {
+    cudaFree(nullptr);   // make sure the current device's context exists
+    cudaGetLastError();
+    const std::pair<const void*, void*> key(table, current_context());
+    std::lock_guard<std::mutex> lk(g_prep_mu);
+    return key.second != nullptr && g_prepared.count(key) != 0;
+}
+
+void mark_context_prepared(const void* table) {
+    const std::pair<const void*, void*> key(table, current_context());
+    if (!key.second) return;
+    std::lock_guard<std::mutex> lk(g_prep_mu);
+    g_prepared.insert(key);
 }
 
 static bool on_device_ptr(const void* ptr) {

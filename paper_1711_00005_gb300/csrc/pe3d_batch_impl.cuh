@@ -22,20 +22,21 @@ struct BatchTable {
     }
 };
 
+// the batched kernels, with their shared-memory limits set once per device context
 template <typename C>
-const BatchTable<C>& batch_kernels() {
+int batch_kernels(const BatchTable<C>** out) {
     static const BatchTable<C> t;
-    static bool attr = false;
-    if (!attr) {
+    if (!context_prepared(&t)) {
         for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b)
-            {
-                cudaFuncSetAttribute(t.k[a][b], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BUDGET);
-                cudaFuncSetAttribute(t.k[a][b], cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+            for (int b = 0; b < 3; ++b) {
+                PE3D_CUDA(cudaFuncSetAttribute(t.k[a][b], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)SMEM_BUDGET));
+                PE3D_CUDA(cudaFuncSetAttribute(t.k[a][b], cudaFuncAttributePreferredSharedMemoryCarveout, 100));
             }
-        attr = true;
+        mark_context_prepared(&t);
     }
-    return t;
+    *out = &t;
+    return PE3D_OK;
 }
 
 inline int batch_class(int L) { return std::max(0, chunk_class(L) - 1); }
@@ -87,7 +88,10 @@ int launch_batched(pe3d_plan_s* owner, std::vector<MarchArgs<C>>& descs, int nst
     unsigned char* b = static_cast<unsigned char*>(*devbuf);
     PE3D_CUDA(cudaMemcpyAsync(b, descs.data(), dbytes, cudaMemcpyHostToDevice, stream));
     PE3D_CUDA(cudaMemcpyAsync(b + dbytes, pref.data(), sizeof(int) * pref.size(), cudaMemcpyHostToDevice, stream));
-    const void* fn = batch_kernels<C>().k[ca][cb];
+    const BatchTable<C>* bt = nullptr;
+    int rc0 = batch_kernels<C>(&bt);
+    if (rc0) return rc0;
+    const void* fn = bt->k[ca][cb];
     int nb = 0;
     PE3D_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, NT, smem));
     if (nb < 1) return fail(PE3D_ERR_ARG, "batched kernel does not fit on an SM");

@@ -142,4 +142,12 @@ int active_slice(const std::vector<double>& slice_r, double r);
 pe3d::MediumStep medium_step(const std::vector<double>& slice_r, double r);   // interpolation at r
 int encode_tmaps(pe3d_plan_s* p);   // tmap_v from v and the layout
 
+// Kernel attributes (the dynamic shared-memory limit, the carveout) belong to a
+// device context.  context_prepared(table) says whether the kernels named by
+// `table` have had them set in the calling thread's current context;
+// mark_context_prepared records that they now have.  Both are thread-safe;
+// two threads preparing the same table at once only set the same values twice.
+bool context_prepared(const void* table);
+void mark_context_prepared(const void* table);
+
 }  // namespace pe3d_host

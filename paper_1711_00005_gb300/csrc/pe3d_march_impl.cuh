@@ -316,11 +316,11 @@ int persistent_grid(const pe3d_plan_s* p, SmemPlan* sp, int* grid) {
     return fail(PE3D_ERR_ARG, "persistent kernel does not fit on an SM");
 }
 
+// Shared-memory limits of every march kernel, set once per device context
 template <typename C>
 int prepare_kernels(const pe3d_plan_s* p) {
-    static bool done = false;
-    if (!done) {
-        const KernelTable<C>& t = kernels<C>();
+    const KernelTable<C>& t = kernels<C>();
+    if (!context_prepared(&t)) {
         for (int a = 0; a < 4; ++a) {
             PE3D_CUDA(cudaFuncSetAttribute(t.A[a], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BUDGET));
             PE3D_CUDA(cudaFuncSetAttribute(t.A[a], cudaFuncAttributePreferredSharedMemoryCarveout, 100));
@@ -336,7 +336,7 @@ int prepare_kernels(const pe3d_plan_s* p) {
                 PE3D_CUDA(cudaFuncSetAttribute(t.persist[a][b], cudaFuncAttributePreferredSharedMemoryCarveout, 100));
             }
         }
-        done = true;
+        mark_context_prepared(&t);
     }
     (void)p;
     return PE3D_OK;

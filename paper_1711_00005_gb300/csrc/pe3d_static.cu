@@ -13,10 +13,12 @@
 // The array is pe3d_static_scratch, PE3D_STATIC_SCRATCH_BYTES (32 MiB) on
 // every GPU that loads this library, held until the process exits.  Host code
 // must not pass the symbol itself to a kernel (on the host it is only a
-// stand-in); the first call on each device looks up its device address with
-// cudaGetSymbolAddress, with that device current, and caches it.
+// stand-in): every call looks up its device address with cudaGetSymbolAddress,
+// with the call's device current.  The lookup is not cached, because the
+// address belongs to the device context: after cudaDeviceReset the module is
+// loaded again and the array may sit elsewhere.  The first call on a device
+// loads the library's device code there.
 #include <cmath>
-#include <mutex>
 #include <string>
 
 #include "pe3d_internal.h"
@@ -25,10 +27,6 @@
 namespace {
 
 static __device__ __align__(256) unsigned char pe3d_static_scratch[PE3D_STATIC_SCRATCH_BYTES];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mu;
-void* g_scratch_addr[kMaxDevices] = {};
 
 struct SliceRanges {
     int K;
@@ -51,20 +49,14 @@ inline size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 template <typename C>
 constexpr bool precision_is_fp32() { return sizeof(C) == 8; }
 
-// Device address of the scratch array on the current device (looked up once).
+// Device address of the scratch array in the current device's context, looked
+// up on every call (cheap once the module is loaded; a cached address would be
+// stale after the context is destroyed and created again).
 int scratch_address(void** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return pe3d_host::cuda_fail(e, "cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices) return pe3d_host::fail(PE3D_ERR_ARG, "device ordinal out of range");
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, pe3d_static_scratch);
-        if (e != cudaSuccess) return pe3d_host::cuda_fail(e, "cudaGetSymbolAddress(pe3d_static_scratch)");
-        g_scratch_addr[dev] = p;
-    }
-    *out = g_scratch_addr[dev];
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, pe3d_static_scratch);
+    if (e != cudaSuccess || !p) return pe3d_host::cuda_fail(e, "cudaGetSymbolAddress(pe3d_static_scratch)");
+    *out = p;
     return PE3D_OK;
 }
 
@@ -230,7 +222,7 @@ extern "C" int pe3d_march_static(int Nz, int Ntheta, double dz, double dtheta, d
                                       std::to_string((size_t)PE3D_STATIC_SCRATCH_BYTES) +
                                       " (PE3D_STATIC_SCRATCH_BYTES); use pe3d_march for larger grids");
 
-    // 2. the device: scratch address (first call per device), pointer checks
+    // 2. the device: scratch address in this context, pointer checks
     void* base = nullptr;
     if ((rc = scratch_address(&base))) return rc;
     int dev = 0;
