@@ -102,6 +102,40 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def live_peaks():
+    """L2 copy bandwidth and FMA rates measured on this GPU now (before the
+    timed region), by the probes of paper_1711_00005_gb300.peaks."""
+    from paper_1711_00005_gb300 import peaks
+    try:
+        return peaks.measure()
+    except Exception as e:          # reported, not fatal: the HBM roofline stands alone
+        return {"error": str(e)}
+
+
+def l2_roofline(achieved_gbs, lp):
+    if not lp or "l2_gbs" not in lp:
+        return None
+    return {"bound": "l2", "achieved": achieved_gbs, "peak": lp["l2_gbs"], "unit": "GB/s",
+            "frac": achieved_gbs / lp["l2_gbs"],
+            "peak_source": "measured in this run: L2-resident read+write copy (pe3d_peak_l2_copy), "
+                           + ", ".join(f"{k} {v:.0f} GB/s" for k, v in lp["l2_by_footprint_gbs"].items())}
+
+
+def fp64_peak(lp):
+    """(TFLOP/s, source) of the FP64 pipe: measured in this run, else nominal."""
+    if lp and lp.get("fp64_tflops"):
+        return lp["fp64_tflops"], "measured in this run (pe3d_peak_fma, FP64 FMA chains)"
+    return NOMINAL_FP64_GFLOPS / 1e3, "nominal FP64 rate of the profiling recipe"
+
+
+def oracle_one_thread(wl, steps, interp=False, taylor=False):
+    """The oracle at one thread on a bounded sample: the first `steps` range
+    steps of the workload."""
+    _, dt = oracle_run(wl, steps, 1, interp, taylor)
+    return {"value": wl.grid.points * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {steps} range steps of {wl.grid.name}, one thread ({dt:.1f} s)"}
+
+
 # the files the range-march kernels are built from
 MARCH_SOURCES = ("pe3d_device.cuh", "pe3d_f32.cu", "pe3d_f64.cu", "pe3d_kernels.cuh", "pe3d_march_impl.cuh")
 
@@ -310,7 +344,9 @@ def run_ours(args):
         ref, dt = oracle_run(wl, g.steps, cores, interp, taylor)
         cpu = {"value": g.points * g.steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"the full {g.steps}-step march of {g.name} (FP64 C oracle, OpenMP over "
-                         f"systems, {dt:.1f} s)"}
+                         f"systems, {dt:.1f} s)",
+               "one_thread": oracle_one_thread(wl, min(g.steps, args.one_thread_steps), interp, taylor)}
+    lp = live_peaks() if rank == 0 else None
 
     stream = torch.cuda.Stream(device=dev)
     n2_dev = torch.from_numpy(wl.n2).to(dev)
@@ -439,15 +475,20 @@ def run_ours(args):
             roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "peak_source": f"{peak_kind} hbm_gbs", "kernel": kname,
                     "algorithmic_bytes_per_launch": bpp * point_steps, "kernel_ms": kns / 1e6,
-                    "traffic": recorded_traffic(kname, g.name)}
+                    "traffic": recorded_traffic(kname, g.name),
+                    # the field stays in L2: the same achieved bytes against the L2 copy rate
+                    "l2": l2_roofline(achieved, lp)}
         elif kns:
             achieved = FLOPS_PER_POINT_STEP * point_steps / (kns * 1e-9) / 1e12
             kname = "k_march_persistent<double2>"
-            roof = {"bound": "alu", "achieved": achieved, "peak": NOMINAL_FP64_GFLOPS / 1e3, "unit": "TFLOP/s",
-                    "frac": achieved / (NOMINAL_FP64_GFLOPS / 1e3),
-                    "peak_source": "nominal FP64 rate of the profiling recipe (no measured FP64 peak)",
+            p64, p64_src = fp64_peak(lp)
+            roof = {"bound": "alu", "achieved": achieved, "peak": p64, "unit": "TFLOP/s",
+                    "frac": achieved / p64, "peak_source": p64_src,
                     "kernel": kname, "algorithmic_flops_per_launch": FLOPS_PER_POINT_STEP * point_steps,
-                    "kernel_ms": kns / 1e6, "traffic": recorded_traffic(kname, g.name)}
+                    "kernel_ms": kns / 1e6, "traffic": recorded_traffic(kname, g.name),
+                    "hbm": {"achieved": BYTES_PER_POINT_STEP[precision] * point_steps / (kns * 1e-9) / 1e9,
+                            "peak": peak, "unit": "GB/s",
+                            "frac": BYTES_PER_POINT_STEP[precision] * point_steps / (kns * 1e-9) / 1e9 / peak}}
         line = {
             "metric": METRIC,
             "value": total_units / t,
@@ -496,11 +537,11 @@ def run_ours(args):
                              "note": "per-march set-up inside pe3d_march, CUDA events on the plan's stream"}
             if interp:
                 fl = SETUP_FLOPS_PER_POINT_STEP * point_steps
+                p64, p64_src = fp64_peak(lp)
                 line["setup"].update({"bound": "alu", "achieved": fl / (sns * 1e-9) / 1e12, "unit": "TFLOP/s",
-                                      "peak": NOMINAL_FP64_GFLOPS / 1e3,
-                                      "frac": fl / (sns * 1e-9) / 1e12 / (NOMINAL_FP64_GFLOPS / 1e3),
-                                      "peak_source": "nominal FP64 rate of the profiling recipe",
-                                      "algorithmic_flops_per_launch": fl})
+                                      "peak": p64, "frac": fl / (sns * 1e-9) / 1e12 / p64,
+                                      "peak_source": p64_src, "algorithmic_flops_per_launch": fl})
+        line["peaks_measured_here"] = lp
         if fp64_value is not None:
             line["fp64_march"] = {"value": fp64_value, "unit": UNIT, "max_rel_l2_vs_oracle": fp64_err}
         print(json.dumps(line), flush=True)
@@ -873,6 +914,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--ref-sample-steps", type=int, default=200)
+    ap.add_argument("--one-thread-steps", type=int, default=20,
+                    help="range steps of the one-thread oracle sample beside the all-core baseline")
     ap.add_argument("--range-steps", type=int, default=0, help="truncate the march (profiling)")
     ap.add_argument("--rc", type=int, default=0, help="FP64 residual correction every K steps (FP32)")
     ap.add_argument("--output", choices=["field", "pressure", "tl"], default="field",

@@ -94,6 +94,14 @@ extern "C" {
 
 #define PE3D_OPT_SCHEME    10   /* one of PE3D_SCHEME_*; allowed only before
                                    pe3d_set_medium                                */
+#define PE3D_OPT_WAIT_LIMIT 11  /* polls before a device-side wait gives up with
+                                   PE3D_ERR_TIMEOUT: the grid barriers of the
+                                   persistent and batched launches and the waits
+                                   for their TMA copies (0: the defaults, about a
+                                   second of waiting).  A small value makes the
+                                   waits give up on purpose, to test failure
+                                   handling; the kernel then lets its copies in
+                                   flight land and returns.                      */
 
 /* depth operator of the range step (pe3d_set_option PE3D_OPT_SCHEME) */
 #define PE3D_SCHEME_PADE   0    /* Eq. 4: [1 + (1/4 -+ d/4) X] (default)           */
@@ -279,7 +287,8 @@ typedef struct pe3d_request {
     int Nz, Ntheta;
     double dz, dtheta, dr, k0;
     int boundary, precision;
-    int rc_every;               /* FP64 residual correction period (FP32 only; 0 = off) */
+    int rc_every;               /* FP64 residual correction every rc_every range steps,
+                                   as PE3D_OPT_RC_EVERY (FP32 only; 0 = off)          */
     const void *n2;             /* complex128 [K][Ntheta][Nz], host memory   */
     const double *slice_r;      /* [K]                                       */
     int K;

@@ -47,6 +47,7 @@ PE3D_OPT_CTAS = 7
 PE3D_OPT_Y_MIDPOINT = 8
 PE3D_OPT_MEDIUM_INTERP = 9
 PE3D_OPT_SCHEME = 10
+PE3D_OPT_WAIT_LIMIT = 11
 PE3D_SCHEME_PADE = 0
 PE3D_SCHEME_TAYLOR = 1
 PE3D_OUT_FIELD = 0

@@ -17,8 +17,17 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpe3d.so")
 SOURCES = ["pe3d_api.cu", "pe3d_f32.cu", "pe3d_f64.cu", "pe3d_server.cu", "pe3d_static.cu",
            "pe3d_batch_f32.cu", "pe3d_batch_f64.cu", "pe3d_synth.cu"]
+# the measured roofline denominators (L2 copy, FMA rates): a separate library
+# that only the benchmark loads
+PEAKS_LIB = os.path.join(HERE, "libpe3d_peaks.so")
+PEAKS_SOURCE = "pe3d_peaks.cu"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",
+# Host code is compiled without floating-point contraction: the range at which
+# a step evaluates the medium, r0 + (j+1) dr, decides which slice is active, and
+# it must round as written (product, then sum) on every host, like the oracle;
+# aarch64 compilers otherwise fuse it into one FMA and can pick the other slice
+# when r* falls on a slice boundary.
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2,-ffp-contract=off", "--expt-relaxed-constexpr",
               "-Xptxas", "-v", "-I", os.path.join(HERE, "..", "include")]
 
 
@@ -30,9 +39,9 @@ def nvcc() -> str:
 
 
 def _stale() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(PEAKS_LIB):
         return True
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(PEAKS_LIB))
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     deps.append(os.path.join(HERE, "..", "include", "pe3d.h"))
     deps.append(os.path.abspath(__file__))
@@ -55,8 +64,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr[-4000:]}")
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
+    with cf.ThreadPoolExecutor(max_workers=len(SOURCES) + 1) as ex:
+        objs = list(ex.map(compile_one, SOURCES + [PEAKS_SOURCE]))
+    peaks_obj = objs.pop()
+    tmp = PEAKS_LIB + ".tmp"
+    r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, peaks_obj, "-cudart", "static", "-lpthread", "-ldl",
+                        "-lrt"], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link of {os.path.basename(PEAKS_LIB)} failed:\n{r.stderr[-4000:]}")
+    os.replace(tmp, PEAKS_LIB)
     tmp = LIB + ".tmp"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static", "-lpthread", "-ldl", "-lrt"]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -302,6 +302,10 @@ int pe3d_set_option(pe3d_plan_t p, int option, int value) {
             if (was != value && p->medium_ready) return slice_setup(p);
             return PE3D_OK;
         }
+        case PE3D_OPT_WAIT_LIMIT:
+            if (value < 0) return fail(PE3D_ERR_ARG, "WAIT_LIMIT must be >= 0");
+            p->wait_limit = value;
+            return PE3D_OK;
         case PE3D_OPT_RC_EVERY:
             if (value < 0) return fail(PE3D_ERR_ARG, "RC_EVERY must be >= 0");
             if (value > 0 && p->precision != PE3D_FP32) return fail(PE3D_ERR_ARG, "residual correction is for FP32 plans");
@@ -328,6 +332,7 @@ int pe3d_get_option(pe3d_plan_t p, int option, int* value) {
         case PE3D_OPT_Y_MIDPOINT: *value = p->y_mid; return PE3D_OK;
         case PE3D_OPT_MEDIUM_INTERP: *value = p->interp; return PE3D_OK;
         case PE3D_OPT_SCHEME: *value = p->scheme; return PE3D_OK;
+        case PE3D_OPT_WAIT_LIMIT: *value = p->wait_limit; return PE3D_OK;
         default: return fail(PE3D_ERR_ARG, "unknown option");
     }
 }

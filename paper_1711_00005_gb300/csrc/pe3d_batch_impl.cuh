@@ -13,12 +13,17 @@ using namespace pe3d;
 template <typename C>
 struct BatchTable {
     const void* k[3][3];
+    // the FP64 residual correction of a batched step (FP32 marches only): one
+    // instantiation at the largest chunks, shorter chunks predicated
+    const void* refine;
     BatchTable() {
 #define PE3D_B(a, b) k[a][b] = (const void*)k_march_batched<C, CHUNK_MAX[a + 1], CHUNK_MAX[b + 1]>
         PE3D_B(0, 0); PE3D_B(0, 1); PE3D_B(0, 2);
         PE3D_B(1, 0); PE3D_B(1, 1); PE3D_B(1, 2);
         PE3D_B(2, 0); PE3D_B(2, 1); PE3D_B(2, 2);
 #undef PE3D_B
+        if constexpr (sizeof(C) == 8) refine = (const void*)k_refine_batched<C, CHUNK_MAX[3], CHUNK_MAX[3]>;
+        else refine = nullptr;
     }
 };
 
@@ -33,6 +38,10 @@ int batch_kernels(const BatchTable<C>** out) {
                                                (int)SMEM_BUDGET));
                 PE3D_CUDA(cudaFuncSetAttribute(t.k[a][b], cudaFuncAttributePreferredSharedMemoryCarveout, 100));
             }
+        if (t.refine) {
+            PE3D_CUDA(cudaFuncSetAttribute(t.refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BUDGET));
+            PE3D_CUDA(cudaFuncSetAttribute(t.refine, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+        }
         mark_context_prepared(&t);
     }
     *out = &t;
@@ -42,7 +51,10 @@ int batch_kernels(const BatchTable<C>** out) {
 inline int batch_class(int L) { return std::max(0, chunk_class(L) - 1); }
 
 // Advance every march i from its current field (w of plans[i]) through steps
-// [j0[i], j1[i]) in one cooperative launch of max(j1 - j0) batched steps.
+// [j0[i], j1[i]) in cooperative launches of max(j1 - j0) batched steps in all:
+// one launch, or, when marches have the FP64 residual correction, one launch
+// up to and including each corrected batched step t, followed by a launch of
+// k_refine_batched for step t.
 // descs: host array already filled by fill_args (snapshots, windows set).
 template <typename C>
 int launch_batched(pe3d_plan_s* owner, std::vector<MarchArgs<C>>& descs, int nsteps, cudaStream_t stream,
@@ -96,13 +108,43 @@ int launch_batched(pe3d_plan_s* owner, std::vector<MarchArgs<C>>& descs, int nst
     PE3D_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, NT, smem));
     if (nb < 1) return fail(PE3D_ERR_ARG, "batched kernel does not fit on an SM");
     const int grid = std::min(nb * owner->num_sms, std::max(pref[n], pref[2 * n + 1]));
-    PE3D_CUDA(cudaMemsetAsync(owner->bar, 0, sizeof(unsigned), stream));
     const MarchArgs<C>* dd = reinterpret_cast<const MarchArgs<C>*>(b);
     const int* dp = reinterpret_cast<const int*>(b + dbytes);
     unsigned* bar = owner->bar;
-    int nn = n, ns = nsteps;
-    void* args[] = {&dd, &nn, &dp, &ns, &bar, &status};
-    PE3D_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(NT), args, smem, stream));
+    int nn = n;
+    // batched steps t whose step j = j0 + t is corrected in some march
+    auto refined = [&](int t) {
+        for (const auto& d : descs)
+            if (d.rc_every > 0 && d.j0 + t < d.j1 && (d.j0 + t + 1) % d.rc_every == 0) return true;
+        return false;
+    };
+    int grid_r = 0;
+    for (int t0 = 0; t0 < nsteps;) {
+        int t1 = t0;
+        while (t1 < nsteps && !refined(t1)) ++t1;
+        const bool corr = t1 < nsteps;
+        const int te = corr ? t1 + 1 : nsteps;
+        PE3D_CUDA(cudaMemsetAsync(owner->bar, 0, sizeof(unsigned), stream));
+        int tb = t0, tend = te;
+        void* args[] = {&dd, &nn, &dp, &tb, &tend, &bar, &status};
+        PE3D_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(NT), args, smem, stream));
+        owner->total_launches += 1;
+        if (corr) {
+            if (!bt->refine) return fail(PE3D_ERR_ARG, "the FP64 residual correction is for FP32 marches");
+            if (!grid_r) {
+                int nr = 0;
+                PE3D_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nr, bt->refine, NT, smem));
+                if (nr < 1) return fail(PE3D_ERR_ARG, "batched correction kernel does not fit on an SM");
+                grid_r = std::min(nr * owner->num_sms, std::max(pref[n], pref[2 * n + 1]));
+            }
+            PE3D_CUDA(cudaMemsetAsync(owner->bar, 0, sizeof(unsigned), stream));
+            int tr = t1;
+            void* rargs[] = {&dd, &nn, &dp, &tr, &bar, &status};
+            PE3D_CUDA(cudaLaunchCooperativeKernel(bt->refine, dim3(grid_r), dim3(NT), rargs, smem, stream));
+            owner->total_launches += 1;
+        }
+        t0 = te;
+    }
     owner->last_grid = grid;
     return PE3D_OK;
 }
@@ -113,9 +155,6 @@ int batched_impl(int n, pe3d_plan_s* const* plans, const void* const* u0, const 
     pe3d_plan_s* owner = plans[0];
     for (int i = 1; i < n; ++i)
         if (plans[i]->stream != owner->stream) return fail(PE3D_ERR_ARG, "batched plans must share one stream");
-    for (int i = 0; i < n; ++i)
-        if (plans[i]->rc_every > 0)
-            return fail(PE3D_ERR_ARG, "the FP64 residual correction runs in single-plan marches only");
     int rc = prepare_kernels<C>(owner);
     if (rc) return rc;
     for (int i = 0; i < n; ++i) PE3D_CUDA(cudaMemsetAsync(plans[i]->status, 0, sizeof(int), owner->stream));
@@ -137,8 +176,10 @@ int batched_impl(int n, pe3d_plan_s* const* plans, const void* const* u0, const 
         descs[i].snap = reinterpret_cast<C*>(out[i]);
         descs[i].snap_ld = p->Nz;
         descs[i].stride = stride[i];
+        descs[i].r0 = r0[i];
         descs[i].j0 = 0;
         descs[i].j1 = steps[i];
+        if (p->rc_every > 0 && steps[i] > 0 && (rc = rc_prepare<C>(p, u0[i], descs[i]))) return rc;
         descs[i].status = owner->status;     // march-time errors are reported through the first plan
         nsteps = std::max(nsteps, steps[i]);
         p->last_exec = PE3D_EXEC_PERSISTENT;
@@ -147,10 +188,10 @@ int batched_impl(int n, pe3d_plan_s* const* plans, const void* const* u0, const 
     if ((rc = launch_multi<SetupBArgs<C>>(owner, bargs, bsteps, k_setupB_multi<C>))) return rc;
     owner->total_launches -= 1;                   // counted below with this call's other launches
     if (owner->timing) PE3D_CUDA(cudaEventRecord(owner->ev0, owner->stream));
-    // up to BATCH_MAX marches per launch; more run as consecutive launches on
-    // the same stream (each reuses the descriptor buffer after the previous one)
-    int groups = 0;
-    for (int b = 0; b < n; b += BATCH_MAX, ++groups) {
+    // up to BATCH_MAX marches per launch group; more run as consecutive groups
+    // on the same stream (each reuses the descriptor buffer after the previous one)
+    const int64_t launches0 = owner->total_launches;
+    for (int b = 0; b < n; b += BATCH_MAX) {
         std::vector<MarchArgs<C>> part(descs.begin() + b, descs.begin() + std::min(n, b + BATCH_MAX));
         int ns = 0;
         for (int i = b; i < std::min(n, b + BATCH_MAX); ++i) ns = std::max(ns, steps[i]);
@@ -160,9 +201,10 @@ int batched_impl(int n, pe3d_plan_s* const* plans, const void* const* u0, const 
         if (rc) return rc;
     }
     if (owner->timing) PE3D_CUDA(cudaEventRecord(owner->ev1, owner->stream));
-    // batched launches, one prologue per march, the azimuth set-up, interpolated depth set-ups
-    owner->last_launches = groups + n + 1 + ninterp;
-    owner->total_launches += owner->last_launches;
+    // batched (and correction) launches, one prologue per march, the azimuth
+    // set-up, interpolated depth set-ups
+    owner->last_launches = (owner->total_launches - launches0) + n + 1 + ninterp;
+    owner->total_launches += n + 1 + ninterp;
     return PE3D_OK;
 }
 
@@ -180,8 +222,10 @@ int serve_begin(pe3d_plan_s* p, const void* u0_dev, double r0, int steps, int st
     desc->snap = reinterpret_cast<C*>(snap_dev);
     desc->snap_ld = p->Nz;
     desc->stride = stride;
+    desc->r0 = r0;
     desc->j0 = 0;
     desc->j1 = 0;
+    if (p->rc_every > 0 && steps > 0 && (rc = rc_prepare<C>(p, u0_dev, *desc))) return rc;
     p->total_launches += 2;
     return PE3D_OK;
 }

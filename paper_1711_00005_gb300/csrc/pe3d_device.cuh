@@ -238,10 +238,13 @@ __shared__ long long pe3d_trace_acc[TRACE_SLOTS + 1];   // [TRACE_SLOTS] holds t
 #define PE3D_MARK(s) do { } while (0)
 #endif
 
-// Bounded wait for an mbarrier phase.  On timeout it records the status,
-// waits once more (bounded) for the copies in flight, and returns false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status, int code) {
-    for (long long i = 0; i < MBAR_SPIN_LIMIT; ++i)
+// Bounded wait for an mbarrier phase: at most `limit` polls.  On timeout it
+// records the status, waits once more for the copies in flight (bounded by
+// MBAR_SPIN_LIMIT whatever `limit` is, so that they land before the CTA
+// leaves), and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status, int code,
+                                                  long long limit = MBAR_SPIN_LIMIT) {
+    for (long long i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     atomicExch(status, code);
     for (long long i = 0; i < MBAR_SPIN_LIMIT; ++i)

@@ -34,6 +34,7 @@ struct pe3d_plan_s {
     int y_mid = 0;                   // Y at the step's midpoint instead of r_{j+1}
     int interp = 0;                  // n^2 interpolated linearly in range, set up every step
     int scheme = PE3D_SCHEME_PADE;   // depth operator: Eq. 4 or the Taylor form of Eq. 3
+    int wait_limit = 0;              // polls of the bounded device waits (0: defaults)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // around the range-step kernels
     cudaEvent_t ev2 = nullptr, ev3 = nullptr;   // around the per-march set-up
     cudaStream_t capture = nullptr;   // private stream for graph capture

@@ -105,6 +105,10 @@ struct MarchArgs {
     C* ut = nullptr;              // uncorrected u^{j+1}               [Nt][ldz]
     C* db = nullptr;              // correction d                      [Nt][ldz]
     double k0 = 0, dz = 0, dr = 0, dtheta = 0, r0 = 0;
+    // polls before a bounded wait gives up (PE3D_OPT_WAIT_LIMIT; the defaults
+    // are about a second of waiting)
+    long long spin_limit = SPIN_LIMIT;     // grid barriers
+    long long mbar_limit = MBAR_SPIN_LIMIT; // mbarrier waits for copies
 };
 
 __host__ __device__ constexpr size_t align128(size_t x) { return (x + 127) & ~size_t(127); }
@@ -215,7 +219,7 @@ __device__ bool computeA(const MarchArgs<C>& P, int base, unsigned char* smem, i
     Aff<C>* scr = reinterpret_cast<Aff<C>*>(smem + P.sp.scrA) + gs * 16;
 
     PE3D_MARK(0);
-    const bool ok = mbar_wait_bounded(mbar, (par >> (MB_A + buf)) & 1u, P.status, ST_TIMEOUT);
+    const bool ok = mbar_wait_bounded(mbar, (par >> (MB_A + buf)) & 1u, P.status, ST_TIMEOUT, P.mbar_limit);
     par ^= 1u << (MB_A + buf);
     par &= ~(1u << (INFLIGHT + MB_A + buf));
     if (!__syncthreads_and(ok)) return false;
@@ -369,7 +373,7 @@ __device__ bool computeA_taylor(const MarchArgs<C>& P, int base, unsigned char* 
     C* sw = reinterpret_cast<C*>(smem + P.sp.a[0] + gs * gstride);
     Aff<C>* scr = reinterpret_cast<Aff<C>*>(smem + P.sp.scrA) + gs * 16;
 
-    const bool ok = mbar_wait_bounded(mbar, (par >> MB_A) & 1u, P.status, ST_TIMEOUT);
+    const bool ok = mbar_wait_bounded(mbar, (par >> MB_A) & 1u, P.status, ST_TIMEOUT, P.mbar_limit);
     par ^= 1u << MB_A;
     par &= ~(1u << (INFLIGHT + MB_A));
     if (!__syncthreads_and(ok)) return false;
@@ -516,7 +520,7 @@ __device__ bool computeB(const MarchArgs<C>& P, int j, int tile, unsigned char* 
         const int r0z = P.nload * P.BY;
         for (int i = r0z * TZ + tid; i < NtP * TZ; i += NT) tl[i] = czero<C>();
     }
-    const bool ok = mbar_wait_bounded(mbar, (par >> (MB_B + buf)) & 1u, P.status, ST_TIMEOUT);
+    const bool ok = mbar_wait_bounded(mbar, (par >> (MB_B + buf)) & 1u, P.status, ST_TIMEOUT, P.mbar_limit);
     par ^= 1u << (MB_B + buf);
     par &= ~(1u << (INFLIGHT + MB_B + buf));
     if (!__syncthreads_and(ok)) return false;
@@ -742,21 +746,23 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
 // Grid-wide barrier for a cooperative launch (all CTAs co-resident), split in
 // two so thread 0 can issue independent copies in between.  Arrive: every
 // thread orders its generic global writes before later async-proxy (TMA)
-// reads, then one release add.  Wait: acquire polls, bounded: after
-// SPIN_LIMIT polls, or once another CTA has flagged an error, it records
-// PE3D_ERR_TIMEOUT and returns false.
+// reads, then one release add.  Wait: acquire polls, bounded: after `limit`
+// polls (SPIN_LIMIT unless the plan sets PE3D_OPT_WAIT_LIMIT), or once
+// another CTA has flagged an error, it records PE3D_ERR_TIMEOUT and returns
+// false.
 __device__ __forceinline__ void grid_arrive(unsigned* ctr) {
     asm volatile("fence.proxy.async.global;" ::: "memory");
     __syncthreads();
     if (threadIdx.x == 0) red_release_add(ctr, 1u);
 }
-__device__ __forceinline__ bool grid_wait(unsigned* ctr, unsigned target, int* status) {
+__device__ __forceinline__ bool grid_wait(unsigned* ctr, unsigned target, int* status,
+                                          long long limit = SPIN_LIMIT) {
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
         int ok = 1;
         long long spins = 0;
         while (ld_acquire(ctr) < target) {
-            if (++spins > SPIN_LIMIT) { atomicExch(status, ST_TIMEOUT); ok = 0; break; }
+            if (++spins > limit) { atomicExch(status, ST_TIMEOUT); ok = 0; break; }
             if ((spins & 255) == 0 && ld_relaxed(status) != ST_OK) { ok = 0; break; }
         }
         asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -765,9 +771,10 @@ __device__ __forceinline__ bool grid_wait(unsigned* ctr, unsigned target, int* s
     __syncthreads();
     return s_ok != 0;
 }
-__device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target, int* status) {
+__device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target, int* status,
+                                             long long limit = SPIN_LIMIT) {
     grid_arrive(ctr);
-    return grid_wait(ctr, target, status);
+    return grid_wait(ctr, target, status, limit);
 }
 
 // ---------------------------------------------------------------------------
@@ -930,7 +937,7 @@ __global__ void __launch_bounds__(NT) k_march_persistent(const __grid_constant__
             if (!ok) PE3D_ABORT();
         }
         PE3D_MARK(16);
-        if (!grid_barrier(P.bar, (++nb) * G, P.status)) PE3D_ABORT();
+        if (!grid_barrier(P.bar, (++nb) * G, P.status, P.spin_limit)) PE3D_ABORT();
         PE3D_MARK(17);
         // phase B (Eq. 6)
         if (hasB) {
@@ -946,11 +953,11 @@ __global__ void __launch_bounds__(NT) k_march_persistent(const __grid_constant__
         grid_arrive(P.bar);
         // the next step's azimuth coefficients, while the barrier completes
         if (threadIdx.x == 0 && hasB && !refine && j + 1 < P.j1) prefetch_coefB(P, j + 1, smem, 0, 0, par);
-        if (!grid_wait(P.bar, (++nb) * G, P.status)) PE3D_ABORT();
+        if (!grid_wait(P.bar, (++nb) * G, P.status, P.spin_limit)) PE3D_ABORT();
         PE3D_MARK(19);
         if (refine) {
             residual_phase(P, j);                                   // r into v
-            if (!grid_barrier(P.bar, (++nb) * G, P.status)) PE3D_ABORT();
+            if (!grid_barrier(P.bar, (++nb) * G, P.status, P.spin_limit)) PE3D_ABORT();
             MarchArgs<C> Q = P;                                    // A^-1 r into v
             Q.w = P.v;
             Q.c1 = czero<C>();
@@ -965,17 +972,17 @@ __global__ void __launch_bounds__(NT) k_march_persistent(const __grid_constant__
                 if (!computeA<C, LA>(Q, u * P.NG, smem, 0, par)) PE3D_ABORT();
             }
             sl_held = -1;
-            if (!grid_barrier(P.bar, (++nb) * G, P.status)) PE3D_ABORT();
+            if (!grid_barrier(P.bar, (++nb) * G, P.status, P.spin_limit)) PE3D_ABORT();
             Q.w = P.db;                                            // B^-1 A^-1 r into db
             for (int t = bid; t < P.tiles; t += G) {
                 if (threadIdx.x == 0) loadB(Q, &P.tmap_v, j, t, smem, 0, true, par);
                 if (!computeB<C, LB>(Q, j, t, smem, 0, 0, par, true)) PE3D_ABORT();
             }
-            if (!grid_barrier(P.bar, (++nb) * G, P.status)) PE3D_ABORT();
+            if (!grid_barrier(P.bar, (++nb) * G, P.status, P.spin_limit)) PE3D_ABORT();
             combine_phase(P, j);
             grid_arrive(P.bar);
             if (threadIdx.x == 0 && hasB && j + 1 < P.j1) prefetch_coefB(P, j + 1, smem, 0, 0, par);
-            if (!grid_wait(P.bar, (++nb) * G, P.status)) PE3D_ABORT();
+            if (!grid_wait(P.bar, (++nb) * G, P.status, P.spin_limit)) PE3D_ABORT();
         }
     }
 }
@@ -999,10 +1006,83 @@ __device__ __forceinline__ int find_march(const int* pref, int n, int u) {
     return lo;
 }
 
+// The FP64 residual correction of batched step t (a launch of its own, after
+// the batched launch that ended with step t), for every march i whose step
+// s_j0[i] + t is corrected (rc_every > 0 and (j + 1) % rc_every == 0): the
+// residual, the solve-only depth and azimuth phases and the FP64 combine, as
+// in the persistent single march, with a grid barrier between them.  Units of
+// the solve-only phases are spread over the CTAs by their batch-wide index.
+// Returns false (all CTAs alike) if a bounded wait gave up.
+template <typename C, int LA, int LB>
+__device__ __forceinline__ bool batched_refine(const MarchArgs<C>* __restrict__ D, int n, const int* s_pa,
+                                               const int* s_pb, const int* s_j0, const int* s_j1, const int* s_rc,
+                                               int t, unsigned char* smem, uint32_t& par, unsigned* bar,
+                                               int* status) {
+    const int G = gridDim.x;
+    const long long lim = D[0].spin_limit;
+    unsigned nb = 0;
+    auto refines = [&](int i) {
+        const int j = s_j0[i] + t;
+        return s_rc[i] > 0 && j < s_j1[i] && (j + 1) % s_rc[i] == 0;
+    };
+    // -1/e of the depth systems: the solve-only pass returns A^-1 r itself
+    auto solve_only = [](MarchArgs<C>& Q) {
+        const double s = 1.0 / ((Q.k0 * Q.dz) * (Q.k0 * Q.dz));
+        const double2 e = make_double2(0.25 * s, -Q.k0 * Q.dr / 4.0 * s);
+        const double en = e.x * e.x + e.y * e.y;
+        Q.c1 = czero<C>();
+        Q.c2p = from64<C>(make_double2(-e.x / en, e.y / en));
+    };
+    for (int i = 0; i < n; ++i)                                   // r into v
+        if (refines(i)) residual_phase(D[i], s_j0[i] + t);
+    if (!grid_barrier(bar, (++nb) * G, status, lim)) return false;
+    for (int u = blockIdx.x; u < s_pa[n]; u += G) {               // A^-1 r into v
+        const int i = find_march(s_pa, n, u);
+        if (!refines(i)) continue;
+        MarchArgs<C> Q = D[i];
+        Q.w = Q.v;
+        solve_only(Q);
+        const int j = s_j0[i] + t, base = (u - s_pa[i]) * Q.NG;
+        if (threadIdx.x == 0) loadA(Q, Q.slice_of_step[j], base, smem, 0, true, par);
+        if (!computeA<C, LA>(Q, base, smem, 0, par)) return false;
+    }
+    if (!grid_barrier(bar, (++nb) * G, status, lim)) return false;
+    for (int u = blockIdx.x; u < s_pb[n]; u += G) {               // B^-1 A^-1 r into db
+        const int i = find_march(s_pb, n, u);
+        if (!refines(i)) continue;
+        MarchArgs<C> Q = D[i];
+        Q.w = Q.db;
+        const int j = s_j0[i] + t, tile = u - s_pb[i];
+        if (threadIdx.x == 0) loadB(Q, &D[i].tmap_v, j, tile, smem, 0, true, par);
+        if (!computeB<C, LB>(Q, j, tile, smem, 0, 0, par, true)) return false;
+    }
+    if (!grid_barrier(bar, (++nb) * G, status, lim)) return false;
+    for (int i = 0; i < n; ++i)                                   // u = u~ + d, the next w
+        if (refines(i)) combine_phase(D[i], s_j0[i] + t);
+    return true;
+}
+
+// One batched step's FP64 residual correction (see batched_refine); launched
+// cooperatively on the batch's grid and shared-memory plan.  One CTA per SM:
+// the kernel runs once every rc_every steps and its long chunks keep all
+// their registers.
+template <typename C, int LA, int LB>
+__global__ void __launch_bounds__(NT, 1) k_refine_batched(const MarchArgs<C>* __restrict__ D, int n,
+                                                       const int* __restrict__ pref, int t, unsigned* bar,
+                                                       int* status) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int s_pa[BATCH_MAX + 1], s_pb[BATCH_MAX + 1], s_j0[BATCH_MAX], s_j1[BATCH_MAX], s_rc[BATCH_MAX];
+    for (int i = threadIdx.x; i <= n; i += NT) { s_pa[i] = pref[i]; s_pb[i] = pref[n + 1 + i]; }
+    for (int i = threadIdx.x; i < n; i += NT) { s_j0[i] = D[i].j0; s_j1[i] = D[i].j1; s_rc[i] = D[i].rc_every; }
+    init_mbarriers(smem);
+    uint32_t par = 0;
+    if (!batched_refine<C, LA, LB>(D, n, s_pa, s_pb, s_j0, s_j1, s_rc, t, smem, par, bar, status)) PE3D_ABORT();
+}
+
 template <typename C, int LA, int LB>
 __global__ void __launch_bounds__(NT, 2) k_march_batched(const MarchArgs<C>* __restrict__ D, int n,
-                                                      const int* __restrict__ pref, int nsteps, unsigned* bar,
-                                                      int* status) {
+                                                      const int* __restrict__ pref, int t_begin, int t_end,
+                                                      unsigned* bar, int* status) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int s_pa[BATCH_MAX + 1], s_pb[BATCH_MAX + 1], s_j0[BATCH_MAX], s_j1[BATCH_MAX];
     for (int i = threadIdx.x; i <= n; i += NT) { s_pa[i] = pref[i]; s_pb[i] = pref[n + 1 + i]; }
@@ -1012,8 +1092,9 @@ __global__ void __launch_bounds__(NT, 2) k_march_batched(const MarchArgs<C>* __r
     uint32_t par = 0;
     const int G = gridDim.x;
     const int nbufA = D[0].sp.nbufA, nbufB = D[0].sp.nbufB;   // one shared-memory plan for the batch
+    const long long lim = D[0].spin_limit;                     // the first plan's wait limit
     unsigned nb = 0;
-    for (int t = 0; t < nsteps; ++t) {
+    for (int t = t_begin; t < t_end; ++t) {
         // the next unit, from u on in steps of G, of a march inside its window
         auto activeA = [&](int u) {
             for (; u < s_pa[n]; u += G) {
@@ -1048,7 +1129,7 @@ __global__ void __launch_bounds__(NT, 2) k_march_batched(const MarchArgs<C>* __r
             [&](int u) { return activeA(u + G); });
         if (!ok) PE3D_ABORT();
         PE3D_MARK(16);
-        if (!grid_barrier(bar, (++nb) * G, status)) PE3D_ABORT();
+        if (!grid_barrier(bar, (++nb) * G, status, lim)) PE3D_ABORT();
         PE3D_MARK(17);
         const int fb = activeB(blockIdx.x);
         if (fb >= 0 && threadIdx.x == 0) loadUB(fb, 0);
@@ -1061,7 +1142,7 @@ __global__ void __launch_bounds__(NT, 2) k_march_batched(const MarchArgs<C>* __r
             [&](int u) { return activeB(u + G); });
         if (!ok) PE3D_ABORT();
         PE3D_MARK(18);
-        if (!grid_barrier(bar, (++nb) * G, status)) PE3D_ABORT();
+        if (!grid_barrier(bar, (++nb) * G, status, lim)) PE3D_ABORT();
         PE3D_MARK(19);
     }
 }

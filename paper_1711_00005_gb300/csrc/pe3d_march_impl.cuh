@@ -238,6 +238,8 @@ void fill_args(pe3d_plan_s* p, MarchArgs<C>& A) {
     A.ut = reinterpret_cast<C*>(p->rc_ut);
     A.db = reinterpret_cast<C*>(p->rc_db);
     A.k0 = p->k0; A.dz = p->dz; A.dr = p->dr; A.dtheta = p->dtheta; A.r0 = 0;
+    A.spin_limit = p->wait_limit > 0 ? p->wait_limit : SPIN_LIMIT;
+    A.mbar_limit = p->wait_limit > 0 ? p->wait_limit : MBAR_SPIN_LIMIT;
 }
 
 // every compiled (depth chunk, azimuth chunk) specialisation
@@ -459,6 +461,29 @@ int step_setup(pe3d_plan_s* p, double r0, int steps, int stride, bool launch_b =
     return PE3D_OK;
 }
 
+// Buffers of the FP64 residual correction (allocated on first use) and its
+// fields in the march's arguments.  A march whose step 0 is corrected
+// (rc_every = 1) needs u^0 in up.
+template <typename C>
+int rc_prepare(pe3d_plan_s* p, const void* u0_dev, MarchArgs<C>& A) {
+    const size_t fb = (size_t)p->Nt * p->ldz * sizeof(C);
+    void** bufs[3] = {&p->rc_up, &p->rc_ut, &p->rc_db};
+    for (void** b : bufs)
+        if (!*b) {
+            int rc = dev_alloc(p, b, fb);
+            if (rc) return rc;
+            PE3D_CUDA(cudaMemsetAsync(*b, 0, fb, p->stream));
+        }
+    A.up = reinterpret_cast<C*>(p->rc_up);
+    A.ut = reinterpret_cast<C*>(p->rc_ut);
+    A.db = reinterpret_cast<C*>(p->rc_db);
+    A.rc_every = p->rc_every;
+    if (p->rc_every == 1)
+        PE3D_CUDA(cudaMemcpy2DAsync(p->rc_up, p->ldz * sizeof(C), u0_dev, p->Nz * sizeof(C), p->Nz * sizeof(C),
+                                    p->Nt, cudaMemcpyDeviceToDevice, p->stream));
+    return PE3D_OK;
+}
+
 template <typename C>
 int launch_prologue(pe3d_plan_s* p, const void* u0_dev, double r0) {
     const double rs = r0 + (p->y_mid ? 0.5 : 1.0) * p->dr;     // where step 0 evaluates Y
@@ -556,23 +581,10 @@ int march(pe3d_plan_s* p, const void* u0_dev, double r0, int steps, int stride, 
     A.stride = stride;
     A.r0 = r0;
     if (p->rc_every > 0 && steps > 0) {
-        // FP64 residual correction: persistent launch only; buffers on first use
+        // FP64 residual correction: persistent launch only
         if (p->exec != PE3D_EXEC_AUTO && p->exec != PE3D_EXEC_PERSISTENT)
             return fail(PE3D_ERR_ARG, "the FP64 residual correction runs in the persistent launch only");
-        const size_t fb = (size_t)p->Nt * p->ldz * sizeof(C);
-        void** bufs[3] = {&p->rc_up, &p->rc_ut, &p->rc_db};
-        for (void** b : bufs)
-            if (!*b) {
-                if ((rc = dev_alloc(p, b, fb))) return rc;
-                PE3D_CUDA(cudaMemsetAsync(*b, 0, fb, p->stream));
-            }
-        A.up = reinterpret_cast<C*>(p->rc_up);
-        A.ut = reinterpret_cast<C*>(p->rc_ut);
-        A.db = reinterpret_cast<C*>(p->rc_db);
-        A.rc_every = p->rc_every;
-        if (p->rc_every == 1)   // step 0 is corrected: its u^j is u0
-            PE3D_CUDA(cudaMemcpy2DAsync(p->rc_up, p->ldz * sizeof(C), u0_dev, p->Nz * sizeof(C),
-                                        p->Nz * sizeof(C), p->Nt, cudaMemcpyDeviceToDevice, p->stream));
+        if ((rc = rc_prepare<C>(p, u0_dev, A))) return rc;
     }
     rc = run_steps<C>(p, A, steps);
     if (rc) return rc;

@@ -107,6 +107,7 @@ static int estimate_bytes(const pe3d_request& r, size_t* out) {
     b += steps * tmp.NtP * es * (r.boundary == PE3D_PERIODIC ? 2 : 1) + steps * (sizeof(pe3d::StepConst) + 4);
     if (r.boundary == PE3D_PERIODIC) b += 2 * steps * tmp.NtP * 16;
     b += (size_t)(r.steps / r.out_stride) * pts * es;
+    if (r.rc_every > 0) b += 3 * field;   // u^j, the uncorrected u^{j+1} and the correction
     *out = b + 4096;
     return PE3D_OK;
 }
@@ -114,6 +115,7 @@ static int estimate_bytes(const pe3d_request& r, size_t* out) {
 bool pe3d_server_s::start(Request* q) {
     const pe3d_request& r = q->r;
     int rc = pe3d_plan(r.Nz, r.Ntheta, r.dz, r.dtheta, r.dr, r.k0, r.boundary, r.precision, stream, &q->plan);
+    if (!rc && r.rc_every > 0) rc = pe3d_set_option(q->plan, PE3D_OPT_RC_EVERY, r.rc_every);
     if (!rc) rc = pe3d_set_medium(q->plan, q->n2.data(), q->slice_r.data(), r.K, 0);
     const size_t es = elem_of(r.precision);
     const size_t fbytes = (size_t)r.Ntheta * r.Nz * es;
@@ -312,7 +314,8 @@ int pe3d_submit(pe3d_server_t s, const pe3d_request* r, uint64_t* id) {
         (r->boundary == PE3D_PERIODIC && r->Ntheta < 3) || !(r->dz > 0) || !(r->dtheta > 0) || !(r->k0 > 0) ||
         !(r->dr != 0))
         return fail(PE3D_ERR_ARG, "invalid request");
-    if (r->rc_every != 0) return fail(PE3D_ERR_ARG, "residual correction is not available in the request loop");
+    if (r->rc_every < 0 || (r->rc_every > 0 && r->precision != PE3D_FP32))
+        return fail(PE3D_ERR_ARG, "rc_every must be >= 0, and the FP64 residual correction is for FP32 requests");
     for (int k = 1; k < r->K; ++k)
         if (!(r->slice_r[k] > r->slice_r[k - 1])) return fail(PE3D_ERR_ARG, "slice ranges must ascend");
     size_t est = 0;

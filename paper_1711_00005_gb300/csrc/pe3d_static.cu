@@ -33,11 +33,14 @@ struct SliceRanges {
     double r[PE3D_STATIC_MAX_SLICES];
 };
 
-// slice_of_step[j]: the last slice k with R_k <= r0 + (j+1) dr, else slice 0
+// slice_of_step[j]: the last slice k with R_k <= r0 + (j+1) dr, else slice 0.
+// r* is rounded as written (product, then sum; no FMA), as the host code and
+// the definition do, so a step whose r* falls on a slice boundary picks the
+// same slice everywhere.
 __global__ void k_static_slice_table(SliceRanges sr, int steps, double r0, double dr, int* sos) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= steps) return;
-    const double r = r0 + (double)(j + 1) * dr;
+    const double r = __dadd_rn(r0, __dmul_rn((double)(j + 1), dr));
     int k = 0;
     for (int i = 0; i < sr.K; ++i)
         if (sr.r[i] <= r) k = i;

@@ -8,9 +8,12 @@ serves them from one fixed scratch array compiled into the library.
 
 These tests call it through the C ABI and check that two calls in a row each
 give what the allocating entry point (pe3d_plan + pe3d_set_medium +
-pe3d_march) gives, within the parity tolerances used everywhere else (1e-10
-for FP64, 2e-5 for FP32), and that a march larger than the array is refused
-with a clear error.  The file is named so that pytest collects it last.
+pe3d_march) gives, and what the FP64 oracle gives, within the parity
+tolerances used everywhere else (1e-10 for FP64, 2e-5 for FP32).  A third
+call repeats the first after the second has left other data in the array: it
+must give the bit-identical result and leave the device's free memory
+unchanged.  A march larger than the array is refused with a clear error.  The
+file is named so that pytest collects it last.
 """
 import numpy as np
 import pytest
@@ -55,11 +58,13 @@ def test_static_march_matches_allocating_march_twice():
     import paper_1711_00005_gb300 as P
     if not torch.cuda.is_available():
         pytest.fail("CUDA device required")
+    import oracle
     cases = [
         (workloads.random_case(200, 64, periodic=False, K=5, steps=12, seed=91, stride=4), False),
         (workloads.random_case(333, 40, periodic=True, K=3, steps=10, seed=92, stride=5), True),
     ]
     stream = torch.cuda.current_stream()
+    inputs, results = [], []
     for wl, fp32 in cases:                       # two calls in a row, each checked
         g = wl.grid
         cdt = torch.complex64 if fp32 else torch.complex128
@@ -73,3 +78,20 @@ def test_static_march_matches_allocating_march_twice():
         got = out.cpu().numpy()
         assert np.all(np.isfinite(got))
         assert _relerr(got, ref) <= TOL[fp32]
+        # and directly against the FP64 oracle, at the same tolerances
+        assert _relerr(got, oracle.march_workload(wl)) <= TOL[fp32]
+        inputs.append((wl, fp32, n2, u0, out))
+        results.append(got)
+    # a third call repeats the first after the second has filled the array with
+    # other data: what a call leaves behind does not change the next result,
+    # and the call takes no device memory
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    wl, fp32, n2, u0, out = inputs[0]
+    g = wl.grid
+    out.fill_(float("nan"))
+    torch.cuda.synchronize()
+    P.pe3d_march_static(*_args(wl, fp32), n2, wl.slice_r, u0, g.r0, g.steps, g.stride, out, stream)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert np.array_equal(out.cpu().numpy(), results[0])
