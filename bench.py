@@ -5,7 +5,8 @@ One bench step = one pass of the whole hot path over the medium-sized
 100 Hz workload (Nz=1067 x Ntheta=256, 2000 range steps, 101 medium slices):
 FP64 coefficient setup of every slice's depth systems (pe3d_set_medium from a
 device-resident n^2), then the march itself (per-step FP64 azimuth setup,
-then the complex-FP32 range steps in one persistent launch), all through the
+then the complex-FP32 range steps in one cooperative launch: the resident
+march, or the persistent one where the autotuner finds it faster), all through the
 library's C ABI.  The metric is grid-point range-steps per second, at a
 relative L2 error against the FP64 oracle that the run measures and reports.
 
@@ -137,7 +138,8 @@ def oracle_one_thread(wl, steps, interp=False, taylor=False):
 
 
 # the files the range-march kernels are built from
-MARCH_SOURCES = ("pe3d_device.cuh", "pe3d_f32.cu", "pe3d_f64.cu", "pe3d_kernels.cuh", "pe3d_march_impl.cuh")
+MARCH_SOURCES = ("pe3d_device.cuh", "pe3d_f32.cu", "pe3d_f64.cu", "pe3d_kernels.cuh", "pe3d_march_impl.cuh",
+                 "pe3d_resident.cuh", "pe3d_resident.cu")
 
 
 def kernel_source_hash() -> str:
@@ -361,8 +363,6 @@ def run_ours(args):
     exec_mode = args.exec
     if taylor:
         P.pe3d_set_option(plan, P.PE3D_OPT_SCHEME, P.PE3D_SCHEME_TAYLOR)
-        if exec_mode in (0, 3):         # per-step launches, replayed from one CUDA graph
-            exec_mode = 2
     P.pe3d_set_option(plan, P.PE3D_OPT_EXEC, exec_mode)
     P.pe3d_set_option(plan, P.PE3D_OPT_TIMING, 1)
     P.pe3d_set_option(plan, P.PE3D_OPT_OUTPUT, out_mode)
@@ -470,8 +470,12 @@ def run_ours(args):
         roof = None
         if kns and fp32:
             achieved = bpp * point_steps / (kns * 1e-9) / 1e9
-            kname = ("k_phaseA_taylor<float2> + k_phaseB<float2> (per-step launches)" if taylor
-                     else "k_march_persistent<float2>")
+            if taylor:
+                kname = ("k_march_persistent<float2> (Taylor form)" if info["exec"] == 3
+                         else "k_phaseA_taylor<float2> + k_phaseB<float2> (per-step launches)")
+            else:
+                kname = "k_march_resident<float2>" if info["exec"] == 4 else "k_march_persistent<float2>"
+
             roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "peak_source": f"{peak_kind} hbm_gbs", "kernel": kname,
                     "algorithmic_bytes_per_launch": bpp * point_steps, "kernel_ms": kns / 1e6,
@@ -506,7 +510,7 @@ def run_ours(args):
                 "workload": g.name, "Nz": g.Nz, "Ntheta": g.Ntheta, "range_steps": g.steps,
                 "medium_slices": len(wl.slice_r), "point_steps_per_march": point_steps,
                 "precision": "complex64 march, FP64 coefficient setup" if fp32 else "complex128",
-                "exec": ["auto", "stream", "graph", "persistent"][info["exec"]],
+                "exec": ["auto", "stream", "graph", "persistent", "resident"][info["exec"]],
                 "fp64_residual_correction_every": args.rc or None,
                 "scheme": ("Taylor form of Eq. 3: [1 -+ (d/2)(X/2 - X^2/8)], two tridiagonal factors"
                            if taylor else "Eq. 4 (Pade)"),
@@ -873,7 +877,7 @@ def run_served(args):
     same = True
     for idx, (wl, out) in sample.items():
         g = grids[idx]
-        with P.Plan.for_grid(g, fp32=True) as plan:
+        with P.Plan.for_grid(g, fp32=True, exec_mode=P.PE3D_EXEC_PERSISTENT) as plan:
             plan.set_medium(wl.n2, wl.slice_r)
             ref = np.zeros((1, g.Ntheta, g.Nz), np.complex64)
             P.pe3d_march(plan.h, wl.u0.astype(np.complex64), g.r0, g.steps, g.steps, ref)
@@ -910,7 +914,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched-25-400Hz", "broadband-120f", "served"],
                     default="medium-100Hz")
-    ap.add_argument("--exec", type=int, default=3, help="1 stream, 2 graph, 3 persistent")
+    ap.add_argument("--exec", type=int, default=0,
+                    help="0 library choice (after --autotune-steps), 1 stream, 2 graph, 3 persistent, 4 resident")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--ref-sample-steps", type=int, default=200)

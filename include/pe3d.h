@@ -67,6 +67,16 @@ extern "C" {
 #define PE3D_EXEC_STREAM      1 /* two kernels per range step, launched in a loop    */
 #define PE3D_EXEC_GRAPH       2 /* the same launches captured once as a CUDA graph   */
 #define PE3D_EXEC_PERSISTENT  3 /* one cooperative kernel for the whole march        */
+#define PE3D_EXEC_RESIDENT    4 /* one cooperative kernel whose CTAs keep the field in
+                                   shared memory: each CTA owns a block of azimuths x
+                                   depths, and a step exchanges two complex numbers per
+                                   system and block instead of moving the field (complex
+                                   FP32, Eq. 4, no correction, no interpolated medium;
+                                   grids whose blocks fit in shared memory).  The
+                                   rounding order differs from the other launches, so
+                                   its fields are not bit-identical to theirs.  AUTO
+                                   picks it only after pe3d_autotune measured it
+                                   faster than the persistent launch for the plan.   */
 
 /* options (pe3d_set_option) */
 #define PE3D_OPT_EXEC      1    /* one of PE3D_EXEC_*                                */
@@ -108,14 +118,16 @@ extern "C" {
 #define PE3D_SCHEME_TAYLOR 1    /* Eq. 3's Taylor form sqrt(1+x) ~ 1 + x/2 - x^2/8
                                    under the same split: [1 -+ (d/2)(X/2 - X^2/8)],
                                    X^2 the square of the discrete X.  Runs in the
-                                   stream and graph launches (PE3D_EXEC_AUTO picks
-                                   the stream launch); not with the persistent
-                                   launch, an interpolated medium, the FP64
-                                   correction or pe3d_march_batched.  Keeps the
-                                   depth multipliers of two factors per slice; a
-                                   depth unit stages three columns per system, and
-                                   pe3d_march refuses (PE3D_ERR_ARG) a layout whose
-                                   unit does not fit in shared memory.           */
+                                   persistent, stream and graph launches
+                                   (PE3D_EXEC_AUTO picks the persistent launch when
+                                   its depth unit fits, else the stream launch);
+                                   not with the resident launch, an interpolated
+                                   medium, the FP64 correction or
+                                   pe3d_march_batched.  Keeps the depth multipliers
+                                   of two factors per slice; a depth unit stages
+                                   three columns per system, and pe3d_march refuses
+                                   (PE3D_ERR_ARG) a layout whose unit does not fit
+                                   in shared memory.                              */
 
 /* stored quantity (pe3d_set_option PE3D_OPT_OUTPUT), Sec. 2 and Fig. 2      */
 #define PE3D_OUT_FIELD     0    /* the envelope u (default)                          */

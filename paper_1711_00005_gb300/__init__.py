@@ -36,6 +36,7 @@ PE3D_EXEC_AUTO = 0
 PE3D_EXEC_STREAM = 1
 PE3D_EXEC_GRAPH = 2
 PE3D_EXEC_PERSISTENT = 3
+PE3D_EXEC_RESIDENT = 4
 
 PE3D_OPT_EXEC = 1
 PE3D_OPT_ZTHREADS = 2

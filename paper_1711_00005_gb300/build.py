@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpe3d.so")
 SOURCES = ["pe3d_api.cu", "pe3d_f32.cu", "pe3d_f64.cu", "pe3d_server.cu", "pe3d_static.cu",
-           "pe3d_batch_f32.cu", "pe3d_batch_f64.cu", "pe3d_synth.cu"]
+           "pe3d_batch_f32.cu", "pe3d_batch_f64.cu", "pe3d_synth.cu", "pe3d_resident.cu",
+           "pe3d_taylor_f32.cu", "pe3d_taylor_f64.cu"]
 # the measured roofline denominators (L2 copy, FMA rates): a separate library
 # that only the benchmark loads
 PEAKS_LIB = os.path.join(HERE, "libpe3d_peaks.so")

@@ -249,7 +249,7 @@ int pe3d_set_option(pe3d_plan_t p, int option, int value) {
     if (!p) return fail(PE3D_ERR_ARG, "plan is NULL");
     switch (option) {
         case PE3D_OPT_EXEC:
-            if (value < PE3D_EXEC_AUTO || value > PE3D_EXEC_PERSISTENT) return fail(PE3D_ERR_ARG, "unknown exec");
+            if (value < PE3D_EXEC_AUTO || value > PE3D_EXEC_RESIDENT) return fail(PE3D_ERR_ARG, "unknown exec");
             p->exec = value;
             return PE3D_OK;
         case PE3D_OPT_ZTHREADS:
@@ -514,7 +514,7 @@ int pe3d_destroy(pe3d_plan_t p) {
     if (p->ev3) cudaEventDestroy(p->ev3);
     if (p->capture) cudaStreamDestroy(p->capture);
     void** bufs[] = {&p->w, &p->v, &p->u0stage, &p->outstage, &p->n2, &p->mz, &p->mB, &p->zsm, &p->batchbuf, &p->rc_up, &p->rc_ut, &p->rc_db,
-                     &p->gscr, &p->sc, (void**)&p->slice_of_step, &p->lerp, &p->mzs, &p->dd, &p->setupbuf, (void**)&p->status,
+                     &p->gscr, &p->sc, (void**)&p->slice_of_step, &p->lerp, &p->mzs, &p->dd, &p->setupbuf, &p->res_buf, (void**)&p->status,
                      (void**)&p->bar};
     for (void** b : bufs)
         if (*b) { cudaFree(*b); *b = nullptr; }
@@ -587,6 +587,25 @@ int pe3d_autotune(pe3d_plan_t p, double r0, int steps) {
         cudaError_t e = cudaMemsetAsync(u0, 0, fbytes, p->stream);
         if (e != cudaSuccess) rc = cuda_fail(e, "memset");
     }
+    // Under AUTO an eligible plan also times the resident march (its layout is
+    // its own); the candidates below then run as persistent launches, and AUTO
+    // keeps whichever was faster.
+    float res_ms = 1e30f;
+    const bool try_resident = !rc && exec0 == PE3D_EXEC_AUTO && resident_eligible(p);
+    if (try_resident) {
+        p->exec = PE3D_EXEC_RESIDENT;
+        p->timing = 0;
+        int r2 = march_f32(p, u0, r0, steps, steps + 1, nullptr, p->Nz);
+        if (r2 == PE3D_OK) {
+            cudaEventRecord(a, p->stream);
+            r2 = march_f32(p, u0, r0, steps, steps + 1, nullptr, p->Nz);
+            cudaEventRecord(b, p->stream);
+            if (r2 == PE3D_OK) r2 = read_status(p);
+            if (r2 == PE3D_OK) cudaEventElapsedTime(&res_ms, a, b);
+        }
+        if (r2 != PE3D_OK) { g_err.clear(); cudaGetLastError(); res_ms = 1e30f; }
+        p->exec = PE3D_EXEC_PERSISTENT;
+    }
     float best = 1e30f;
     int bestT = T0, bestTZ = TZ0, bestC = p->ctas_per_sm;
     const int Ts[4] = {32, 64, 128, 256}, TZs[5] = {2, 4, 8, 16, 32};
@@ -621,6 +640,7 @@ int pe3d_autotune(pe3d_plan_t p, double r0, int steps) {
         }
     }
     p->ctas_per_sm = bestC;
+    if (try_resident) p->prefer_resident = res_ms <= best ? 1 : 0;
     if (u0) dev_free(p, &u0, fbytes);
     cudaEventDestroy(a);
     cudaEventDestroy(b);

@@ -155,8 +155,7 @@ int batched_impl(int n, pe3d_plan_s* const* plans, const void* const* u0, const 
     pe3d_plan_s* owner = plans[0];
     for (int i = 1; i < n; ++i)
         if (plans[i]->stream != owner->stream) return fail(PE3D_ERR_ARG, "batched plans must share one stream");
-    int rc = prepare_kernels<C>(owner);
-    if (rc) return rc;
+    int rc = PE3D_OK;
     for (int i = 0; i < n; ++i) PE3D_CUDA(cudaMemsetAsync(plans[i]->status, 0, sizeof(int), owner->stream));
     std::vector<MarchArgs<C>> descs(n);
     std::vector<SetupBArgs<C>> bargs;

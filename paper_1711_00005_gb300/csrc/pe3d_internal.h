@@ -35,6 +35,7 @@ struct pe3d_plan_s {
     int interp = 0;                  // n^2 interpolated linearly in range, set up every step
     int scheme = PE3D_SCHEME_PADE;   // depth operator: Eq. 4 or the Taylor form of Eq. 3
     int wait_limit = 0;              // polls of the bounded device waits (0: defaults)
+    int prefer_resident = 0;         // AUTO runs the resident march (set by pe3d_autotune when it measured it faster)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // around the range-step kernels
     cudaEvent_t ev2 = nullptr, ev3 = nullptr;   // around the per-march set-up
     cudaStream_t capture = nullptr;   // private stream for graph capture
@@ -79,6 +80,8 @@ struct pe3d_plan_s {
     size_t batchbuf_bytes = 0;
     void* setupbuf = nullptr;         // multi-plan set-up descriptors (when this plan leads one)
     size_t setupbuf_bytes = 0;
+    void* res_buf = nullptr;          // resident march: exchange words and azimuth-block constants
+    size_t res_bytes = 0;
     int* status = nullptr;            // device status word
     unsigned* bar = nullptr;          // grid-barrier counter
     bool medium_ready = false;
@@ -119,7 +122,7 @@ int batched_f64(int n, pe3d_plan_s* const* plans, const void* const* u0, const d
                 const int* stride, void* const* out);
 
 }  // namespace pe3d_host
-namespace pe3d { struct SmemPlan; }
+namespace pe3d { struct SmemPlan; template <typename C> struct MarchArgs; }
 namespace pe3d_host {
 // grid and shared-memory plan of the persistent march for a laid-out plan
 void persistent_config_f32(const pe3d_plan_s* p, pe3d::SmemPlan* sp, int* grid);
@@ -133,6 +136,15 @@ struct StaticKernels {
     const void* persist[4][4];
 };
 int static_kernels_f32(StaticKernels* k);   // also sets their shared-memory limits
+
+// the resident march (pe3d_resident.cu): whether a plan can take it, and its
+// launch for steps [0, steps) from w^0 in A.w
+bool resident_eligible(const pe3d_plan_s* p);
+// the persistent kernels of the Taylor form (pe3d_taylor_f32.cu, pe3d_taylor_f64.cu)
+// for depth / azimuth chunk classes ca, cb; nullptr on error
+const void* taylor_persistent_f32(int ca, int cb);
+const void* taylor_persistent_f64(int ca, int cb);
+int resident_launch_f32(pe3d_plan_s* p, const pe3d::MarchArgs<float2>& A, int steps);
 int static_kernels_f64(StaticKernels* k);
 
 // shared helpers (pe3d_api.cu)

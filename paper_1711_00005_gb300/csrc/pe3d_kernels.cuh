@@ -903,7 +903,10 @@ __device__ __forceinline__ bool unit_pipeline(int first, int nbuf, Load load, Co
     return true;
 }
 
-template <typename C, int LA, int LB>
+// TAYLOR: the Taylor form of Eq. 3 (depth units of three columns, both
+// factors solved from the same w; one buffer, no kept multipliers; no FP64
+// correction)
+template <typename C, int LA, int LB, bool TAYLOR = false>
 __global__ void __launch_bounds__(NT) k_march_persistent(const __grid_constant__ MarchArgs<C> P) {
     extern __shared__ __align__(128) unsigned char smem[];
     init_mbarriers(smem);
@@ -913,7 +916,7 @@ __global__ void __launch_bounds__(NT) k_march_persistent(const __grid_constant__
     unsigned nb = 0;
     const int unitsA = (P.Nt + P.NG - 1) / P.NG;
     const bool hasA = bid < unitsA, hasB = bid < P.tiles;
-    const bool keepA = P.sp.keepA && unitsA <= G;     // one depth unit per CTA
+    const bool keepA = !TAYLOR && P.sp.keepA && unitsA <= G;     // one depth unit per CTA
     // thread 0 reads the next step's slice one step ahead
     int sl_next = (threadIdx.x == 0 && P.j0 < P.j1) ? P.slice_of_step[P.j0] : 0;
     int sl_held = -1;                                 // slice of the multipliers in a[0] (keepA)
@@ -923,18 +926,27 @@ __global__ void __launch_bounds__(NT) k_march_persistent(const __grid_constant__
     for (int j = P.j0; j < P.j1; ++j) {
         const int sl = sl_next;
         // phase A (Eq. 5)
-        if (hasA && threadIdx.x == 0) {
-            loadA(P, sl, bid * P.NG, smem, 0, !(keepA && sl == sl_held), par);
-            sl_held = keepA ? sl : -1;
-        }
-        // read after the copies are issued: their proxy fence would wait for it
-        if (threadIdx.x == 0 && j + 1 < P.j1) sl_next = P.slice_of_step[j + 1];
-        if (hasA) {
-            const bool ok = unit_pipeline(
-                bid, P.sp.nbufA,
-                [&](int u, int b) { loadA(P, sl, u * P.NG, smem, b, true, par); },
-                [&](int u, int b) { return computeA<C, LA>(P, u * P.NG, smem, b, par); }, nextA);
-            if (!ok) PE3D_ABORT();
+        if constexpr (TAYLOR) {
+            if (hasA && threadIdx.x == 0) loadA_taylor(P, sl, bid * P.NG, smem, par);
+            if (threadIdx.x == 0 && j + 1 < P.j1) sl_next = P.slice_of_step[j + 1];
+            for (int u = bid; u < unitsA; u += G) {
+                if (!computeA_taylor<C, LA>(P, u * P.NG, smem, par)) PE3D_ABORT();   // returns with the buffer free
+                if (threadIdx.x == 0 && u + G < unitsA) loadA_taylor(P, sl, (u + G) * P.NG, smem, par);
+            }
+        } else {
+            if (hasA && threadIdx.x == 0) {
+                loadA(P, sl, bid * P.NG, smem, 0, !(keepA && sl == sl_held), par);
+                sl_held = keepA ? sl : -1;
+            }
+            // read after the copies are issued: their proxy fence would wait for it
+            if (threadIdx.x == 0 && j + 1 < P.j1) sl_next = P.slice_of_step[j + 1];
+            if (hasA) {
+                const bool ok = unit_pipeline(
+                    bid, P.sp.nbufA,
+                    [&](int u, int b) { loadA(P, sl, u * P.NG, smem, b, true, par); },
+                    [&](int u, int b) { return computeA<C, LA>(P, u * P.NG, smem, b, par); }, nextA);
+                if (!ok) PE3D_ABORT();
+            }
         }
         PE3D_MARK(16);
         if (!grid_barrier(P.bar, (++nb) * G, P.status, P.spin_limit)) PE3D_ABORT();
@@ -955,6 +967,7 @@ __global__ void __launch_bounds__(NT) k_march_persistent(const __grid_constant__
         if (threadIdx.x == 0 && hasB && !refine && j + 1 < P.j1) prefetch_coefB(P, j + 1, smem, 0, 0, par);
         if (!grid_wait(P.bar, (++nb) * G, P.status, P.spin_limit)) PE3D_ABORT();
         PE3D_MARK(19);
+        if constexpr (!TAYLOR) {
         if (refine) {
             residual_phase(P, j);                                   // r into v
             if (!grid_barrier(P.bar, (++nb) * G, P.status, P.spin_limit)) PE3D_ABORT();
@@ -983,6 +996,7 @@ __global__ void __launch_bounds__(NT) k_march_persistent(const __grid_constant__
             grid_arrive(P.bar);
             if (threadIdx.x == 0 && hasB && j + 1 < P.j1) prefetch_coefB(P, j + 1, smem, 0, 0, par);
             if (!grid_wait(P.bar, (++nb) * G, P.status, P.spin_limit)) PE3D_ABORT();
+        }
         }
     }
 }

@@ -290,27 +290,45 @@ SmemPlan single_unit_plan(const pe3d_plan_s* p) {
 // Grid and shared-memory plan of the persistent march with `per` CTAs per
 // SM (or one per unit when there are fewer): units beyond the grid are
 // double-buffered when the buffers fit, and a CTA with a single depth unit
-// keeps its multipliers in shared memory.
+// keeps its multipliers in shared memory.  The Taylor form's depth units
+// (three columns per system) take one buffer and keep nothing; sp->total = 0
+// when they do not fit.
 template <typename C>
 void persistent_config_n(const pe3d_plan_s* p, int per, SmemPlan* sp, int* grid) {
     const int unitsA = (p->Nt + p->NG - 1) / p->NG;
     const size_t budget = per == 2 ? SMEM_HALF : SMEM_BUDGET;
     const int G = std::min(per * p->num_sms, std::max(unitsA, p->tiles));
+    *grid = G;
+    if (p->scheme == PE3D_SCHEME_TAYLOR) {
+        if (!plan_smem_sizes<C>((size_t)p->NG * grpA3_bytes<C>(p->ldz), tile_bytes<C>(p->rowsB, p->TZ),
+                                coef_bytes<C>(p->NtP, p->boundary == PE3D_PERIODIC), p->NG, p->TZ, false,
+                                p->tiles > G, false, true, budget, sp))
+            sp->total = 0;
+        return;
+    }
     if (!plan_smem<C>(p->NG, p->ldz, p->rowsB, p->TZ, p->NtP, p->boundary == PE3D_PERIODIC, unitsA > G,
                       p->tiles > G, unitsA <= G, true, budget, sp))
         *sp = single_unit_plan<C>(p);
-    *grid = G;
 }
+
+template <typename C> const void* taylor_persistent(int ca, int cb);
+template <> inline const void* taylor_persistent<float2>(int ca, int cb) { return taylor_persistent_f32(ca, cb); }
+template <> inline const void* taylor_persistent<double2>(int ca, int cb) { return taylor_persistent_f64(ca, cb); }
 template <typename C>
 void persistent_config(const pe3d_plan_s* p, SmemPlan* sp, int* grid) { persistent_config_n<C>(p, 1, sp, grid); }
 
 // The plan's CTAs per SM (ctas_per_sm, 1 by default) if the kernel fits that
 // many on an SM, else one.
 template <typename C>
-int persistent_grid(const pe3d_plan_s* p, SmemPlan* sp, int* grid) {
-    const void* fn = kernels<C>().persist[chunk_class(p->L)][chunk_class(p->Lt)];
+int persistent_grid(const pe3d_plan_s* p, SmemPlan* sp, int* grid, const void** kernel) {
+    const bool taylor = p->scheme == PE3D_SCHEME_TAYLOR;
+    const void* fn = taylor ? taylor_persistent<C>(chunk_class(p->L), chunk_class(p->Lt))
+                            : kernels<C>().persist[chunk_class(p->L)][chunk_class(p->Lt)];
+    if (!fn) return PE3D_ERR_CUDA;
+    *kernel = fn;
     for (int per = p->ctas_per_sm == 2 ? 2 : 1; per >= 1; --per) {
         persistent_config_n<C>(p, per, sp, grid);
+        if (sp->total == 0) continue;          // the Taylor form's depth unit does not fit
         int nb = 0;
         PE3D_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, NT, sp->total));
         if (nb >= per) return PE3D_OK;
@@ -500,10 +518,33 @@ int launch_prologue(pe3d_plan_s* p, const void* u0_dev, double r0) {
 template <typename C>
 int run_steps(pe3d_plan_s* p, MarchArgs<C>& A, int steps) {
     const bool taylor = p->scheme == PE3D_SCHEME_TAYLOR;
+    constexpr bool fp32 = sizeof(C) == 8;
     int exec = p->exec;
-    if (exec == PE3D_EXEC_AUTO) exec = taylor ? PE3D_EXEC_STREAM : PE3D_EXEC_PERSISTENT;
-    if (taylor && exec == PE3D_EXEC_PERSISTENT)
-        return fail(PE3D_ERR_ARG, "the Taylor form runs in the stream and graph launches");
+    if (exec == PE3D_EXEC_AUTO) {
+        if (taylor) {   // persistent when its three-column depth unit fits, else per-step launches
+            int g = 0;
+            SmemPlan sp;
+            persistent_config_n<C>(p, 1, &sp, &g);
+            exec = sp.total ? PE3D_EXEC_PERSISTENT : PE3D_EXEC_STREAM;
+        } else {
+            exec = fp32 && p->prefer_resident && resident_eligible(p) ? PE3D_EXEC_RESIDENT : PE3D_EXEC_PERSISTENT;
+        }
+    }
+    if (exec == PE3D_EXEC_RESIDENT) {
+        if (!fp32 || !resident_eligible(p))
+            return fail(PE3D_ERR_ARG, "the resident march takes complex-FP32 Eq. 4 marches without the correction or "
+                                      "an interpolated medium, on grids whose blocks fit in shared memory");
+        p->last_exec = exec;
+        if (steps == 0) { p->last_launches = 0; return PE3D_OK; }
+        if (p->timing) PE3D_CUDA(cudaEventRecord(p->ev0, p->stream));
+        if constexpr (fp32) {
+            int rc = resident_launch_f32(p, A, steps);
+            if (rc) return rc;
+        }
+        if (p->timing) PE3D_CUDA(cudaEventRecord(p->ev1, p->stream));
+        p->last_launches = 2;   // azimuth-block constants, the march
+        return PE3D_OK;
+    }
     p->last_exec = exec;
     const int unitsA = (p->Nt + p->NG - 1) / p->NG;
     const KernelTable<C>& kt = kernels<C>();
@@ -512,14 +553,14 @@ int run_steps(pe3d_plan_s* p, MarchArgs<C>& A, int steps) {
     if (p->timing) PE3D_CUDA(cudaEventRecord(p->ev0, p->stream));
     if (exec == PE3D_EXEC_PERSISTENT) {
         int grid = 0;
-        int rc = persistent_grid<C>(p, &A.sp, &grid);
+        const void* fn = nullptr;
+        int rc = persistent_grid<C>(p, &A.sp, &grid, &fn);
         if (rc) return rc;
         p->last_grid = grid;
         PE3D_CUDA(cudaMemsetAsync(p->bar, 0, sizeof(unsigned), p->stream));
         A.j0 = 0; A.j1 = steps;
         void* args[] = {&A};
-        PE3D_CUDA(cudaLaunchCooperativeKernel(kt.persist[ca][cb], dim3(grid), dim3(NT), args, A.sp.total,
-                                              p->stream));
+        PE3D_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(NT), args, A.sp.total, p->stream));
         p->last_launches = 1;
         if (p->timing) PE3D_CUDA(cudaEventRecord(p->ev1, p->stream));
         return PE3D_OK;

@@ -2,17 +2,23 @@
 // marches (the paper's multi-frequency farm, Fig. 2's frequency loop, Sec.
 // 3.2.3) on one GPU.
 //
-// A scheduler thread owns one CUDA stream.  Each turn of its loop it
-//   1. admits queued requests in arrival order while the device-memory budget
-//      and the active-march limit allow (plan, medium upload with FP64
-//      setup, per-step azimuth setup, prologue);
-//   2. advances every admitted march by up to `chunk` range steps in shared
-//      batched launches (one per precision, at most 64 marches each);
-//   3. retires finished marches: copies their snapshots to host memory and
-//      releases their device memory, so waiting requests can be admitted.
-// Requests that arrive while others run join at the next turn.  The
-// per-system arithmetic does not depend on who else is in the batch, so a
-// request's result is the same alone and in the mix.
+// Two host threads:
+//   * the admission thread takes queued requests in arrival order while the
+//     device-memory budget and the active-march limit allow, and sets each up
+//     on a stream of its own (plan, medium upload with FP64 set-up, per-step
+//     azimuth set-up, prologue, status check), then hands it to the
+//     scheduler's ready list;
+//   * the scheduler thread owns the batch stream.  Each turn it moves ready
+//     requests into the batch, advances every admitted march by up to `chunk`
+//     range steps in shared batched launches (one per precision, at most 64
+//     marches each), and retires finished marches (copies their snapshots to
+//     host memory and releases their device memory, so waiting requests can
+//     be admitted).
+// A request's set-up thus never stalls the marches already running: the
+// scheduler waits on nothing but its own launches.  Requests that arrive
+// while others run join at the turn after their set-up ends.  The per-system
+// arithmetic does not depend on who else is in the batch, so a request's
+// result is the same alone and in the mix.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -51,6 +57,7 @@ struct Request {
     double t_submit = 0, t_start = 0, t_done = 0;
     size_t est_bytes = 0;
     pe3d_plan_t plan = nullptr;
+    cudaStream_t stream = nullptr;        // the request's set-up stream
     void* u0_dev = nullptr;
     void* snap_dev = nullptr;
     size_t snap_bytes = 0;
@@ -71,12 +78,16 @@ struct pe3d_server_s {
     int device = 0;
     cudaStream_t stream = nullptr;
     pe3d_plan_t owner = nullptr;          // barrier, status and descriptor buffer of the batched launches
-    std::thread th;
+    std::thread th;                       // scheduler
+    std::thread admit_th;                 // admission
     std::mutex mu;
-    std::condition_variable cv;
+    std::condition_variable cv;           // wakes the admission thread (new request, freed memory, stop)
+    std::condition_variable cv_ready;     // wakes the scheduler (a request is set up, stop)
     bool stop = false;
     std::deque<Request*> pending;
+    std::deque<Request*> ready;           // set up, joining the batch at the next turn
     std::vector<Request*> active;
+    int setting_up = 0;
     std::unordered_map<uint64_t, std::unique_ptr<Request>> all;
     uint64_t next_id = 1;
     size_t used = 0;
@@ -87,6 +98,7 @@ struct pe3d_server_s {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
     void loop();
+    void admit_loop();
     bool start(Request* q);
     void finish(Request* q, bool ok, const std::string& why);
     bool tick();
@@ -112,8 +124,17 @@ static int estimate_bytes(const pe3d_request& r, size_t* out) {
     return PE3D_OK;
 }
 
+// Set a request up on its own stream (admission thread); true when it can join
+// the batch.  Ends with a synchronisation of that stream only.
 bool pe3d_server_s::start(Request* q) {
     const pe3d_request& r = q->r;
+    cudaError_t se = cudaStreamCreateWithFlags(&q->stream, cudaStreamNonBlocking);
+    if (se != cudaSuccess) {
+        q->stream = nullptr;
+        finish(q, false, std::string("request stream: ") + cudaGetErrorString(se));
+        return false;
+    }
+    cudaStream_t stream = q->stream;
     int rc = pe3d_plan(r.Nz, r.Ntheta, r.dz, r.dtheta, r.dr, r.k0, r.boundary, r.precision, stream, &q->plan);
     if (!rc && r.rc_every > 0) rc = pe3d_set_option(q->plan, PE3D_OPT_RC_EVERY, r.rc_every);
     if (!rc) rc = pe3d_set_medium(q->plan, q->n2.data(), q->slice_r.data(), r.K, 0);
@@ -161,6 +182,10 @@ void pe3d_server_s::finish(Request* q, bool ok, const std::string& why) {
         dev_free(q->plan, &q->snap_dev, 0);
         pe3d_destroy(q->plan);
         q->plan = nullptr;
+    }
+    if (q->stream) {
+        cudaStreamDestroy(q->stream);
+        q->stream = nullptr;
     }
     std::lock_guard<std::mutex> lk(mu);
     used -= std::min(used, q->est_bytes);
@@ -244,38 +269,62 @@ bool pe3d_server_s::tick() {
     if (!ok) {   // clear the status word for the next batch
         cudaMemset(owner->status, 0, sizeof(int));
     }
+    if (!done.empty()) cv.notify_all();   // memory freed: the admission thread may take the next request
     return true;
 }
 
+// Admission thread: in arrival order, while the budget and the active-march
+// limit allow (a request larger than the budget still runs when nothing else
+// holds memory), set the next request up and put it on the ready list.
+void pe3d_server_s::admit_loop() {
+    cudaSetDevice(device);
+    for (;;) {
+        Request* q = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            cv.wait(lk, [&] {
+                if (stop) return true;
+                if (pending.empty()) return false;
+                const int in_flight = (int)active.size() + (int)ready.size() + setting_up;
+                const bool empty = in_flight == 0;
+                return in_flight < max_active && (used + pending.front()->est_bytes <= budget || empty);
+            });
+            if (stop) return;
+            q = pending.front();
+            pending.pop_front();
+            used += q->est_bytes;
+            q->state = PE3D_REQ_RUNNING;
+            q->t_start = now();
+            ++n_admitted;
+            ++setting_up;
+        }
+        const bool ok = start(q);
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            --setting_up;
+            if (ok) ready.push_back(q);
+        }
+        cv_ready.notify_all();
+        cv.notify_all();   // a failed set-up released its memory
+    }
+}
+
+// Scheduler thread: join the ready requests, one turn of the batched march,
+// retire; wait when there is nothing to march.
 void pe3d_server_s::loop() {
     cudaSetDevice(device);
     for (;;) {
-        // 1. admission, in arrival order, within the memory budget
-        for (;;) {
-            Request* q = nullptr;
-            {
-                std::unique_lock<std::mutex> lk(mu);
-                if (stop) return;
-                if (!pending.empty() && (int)active.size() < max_active &&
-                    (used + pending.front()->est_bytes <= budget || active.empty())) {
-                    q = pending.front();
-                    pending.pop_front();
-                    used += q->est_bytes;
-                    q->state = PE3D_REQ_RUNNING;
-                    q->t_start = now();
-                    ++n_admitted;
-                }
-            }
-            if (!q) break;
-            if (start(q)) {
-                std::lock_guard<std::mutex> lk(mu);
-                active.push_back(q);
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            if (stop) return;
+            while (!ready.empty()) {
+                active.push_back(ready.front());
+                ready.pop_front();
             }
         }
-        // 2-3. one turn of the batched march, or wait for work
         if (!tick()) {
             std::unique_lock<std::mutex> lk(mu);
-            cv.wait_for(lk, std::chrono::milliseconds(5), [&] { return stop || !pending.empty(); });
+            cv_ready.wait_for(lk, std::chrono::milliseconds(5), [&] { return stop || !ready.empty(); });
             if (stop) return;
         }
     }
@@ -301,6 +350,7 @@ int pe3d_server_create(size_t mem_budget, int max_active, int chunk, pe3d_server
     if (rc) { cudaStreamDestroy(s->stream); return rc; }
     pe3d_server_s* raw = s.release();
     raw->th = std::thread([raw] { raw->loop(); });
+    raw->admit_th = std::thread([raw] { raw->admit_loop(); });
     *out = raw;
     return PE3D_OK;
 }
@@ -389,7 +439,9 @@ int pe3d_server_destroy(pe3d_server_t s) {
         s->stop = true;
     }
     s->cv.notify_all();
+    s->cv_ready.notify_all();
     if (s->th.joinable()) s->th.join();
+    if (s->admit_th.joinable()) s->admit_th.join();
     for (auto& kv : s->all) {
         Request* q = kv.second.get();
         if (q->plan) {
@@ -397,6 +449,7 @@ int pe3d_server_destroy(pe3d_server_t s) {
             dev_free(q->plan, &q->snap_dev, 0);
             pe3d_destroy(q->plan);
         }
+        if (q->stream) cudaStreamDestroy(q->stream);
     }
     if (s->owner) pe3d_destroy(s->owner);
     if (s->stream) cudaStreamDestroy(s->stream);

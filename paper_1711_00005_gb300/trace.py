@@ -34,6 +34,13 @@ NAMES = {
     8: "B: before tile", 9: "B: TMA wait", 10: "B: F1", 11: "B: scan1", 12: "B: F2+B1", 13: "B: scan2",
     14: "B: B2+SM+sync", 15: "B: epilogue", 18: "B: after tiles", 19: "barrier 2",
 }
+# the resident march (exec 4)
+NAMES_RESIDENT = {
+    20: "step start (coefficient copies)", 0: "slice change", 1: "A: zero-carry solve + publish",
+    2: "A: exchange + sweep", 3: "A: sync", 4: "A: carried solve + v", 5: "coefficients wait + sync",
+    6: "B: zero-carry solve + publish", 7: "B: exchange + sweep", 8: "B: sync", 9: "B: carried solve + u",
+    10: "B: sync", 11: "B: stencil + snapshot", 12: "B: w + syncs",
+}
 
 
 def build_traced() -> str:
@@ -60,7 +67,7 @@ def main(argv=None):
                     default="medium-100Hz")
     ap.add_argument("--members", type=int, default=32, help="batched: the highest-frequency members only")
     ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--exec", type=int, default=3, help="1 stream, 3 persistent")
+    ap.add_argument("--exec", type=int, default=3, help="1 stream, 3 persistent, 4 resident")
     ap.add_argument("--autotune-steps", type=int, default=100, help="choose the layout as bench.py does (0: off)")
     a = ap.parse_args(argv)
     import torch
@@ -71,6 +78,8 @@ def main(argv=None):
 
     L = P.load_library(build_traced())
     L.pe3d_trace_read.argtypes = [ctypes.c_void_p, ctypes.c_size_t]
+    L.pe3d_trace_read_resident.argtypes = [ctypes.c_void_p, ctypes.c_size_t]
+    read = L.pe3d_trace_read_resident if a.exec == 4 else L.pe3d_trace_read
     if a.workload in ("batched-25-400Hz", "served-mix"):
         return trace_batched(P, L, workloads, a)
     make = workloads.config2 if a.workload == "medium-100Hz" else workloads.config3
@@ -83,22 +92,22 @@ def main(argv=None):
     u0 = torch.from_numpy(wl.u0.astype(np.complex64)).cuda()
     buf = np.zeros((4096, SLOTS), np.int64)
     plan.march(u0, g.r0, g.steps, g.steps)          # warm-up, then clear the counters
-    L.pe3d_trace_read(buf.ctypes.data, buf.nbytes)
+    read(buf.ctypes.data, buf.nbytes)
     plan.march(u0, g.r0, g.steps, g.steps)
-    L.pe3d_trace_read(buf.ctypes.data, buf.nbytes)
+    read(buf.ctypes.data, buf.nbytes)
     inf = plan.info()
-    G = inf["grid"] if a.exec == 3 else 4096
+    G = inf["grid"] if a.exec in (3, 4) else 4096
     rows = buf[:G]
     rows = rows[rows.sum(axis=1) != 0]
     print("workload", g.name, "layout", {k: inf[k] for k in ("ldz", "zthreads", "zchunk", "ttile", "tchunk", "grid")})
-    report(rows, g.steps)
+    report(rows, g.steps, NAMES_RESIDENT if a.exec == 4 else NAMES)
     plan.close()
 
 
-def report(rows, steps):
+def report(rows, steps, names=NAMES):
     print(f"{'interval':18s} {'mean':>8s} {'max':>8s}   (SM cycles per range step, over {len(rows)} CTAs)")
     tot = 0.0
-    for s_, name in NAMES.items():
+    for s_, name in names.items():
         v = rows[:, s_] / steps
         tot += v.mean()
         print(f"{name:18s} {v.mean():8.0f} {v.max():8.0f}")

@@ -51,17 +51,18 @@ def test_config3_periodic_200Hz_full(P, oracle_lib):
     t = time.perf_counter()
     ref = oracle_lib.march(g, wl.n2, wl.slice_r, wl.u0)
     t_or = time.perf_counter() - t
-    with P.Plan.for_grid(g, fp32=True) as plan:
-        plan.set_medium(torch.from_numpy(wl.n2).cuda(), wl.slice_r)
-        got = plan.march(torch.from_numpy(wl.u0.astype(np.complex64)).cuda(), g.r0, g.steps, g.stride)
-        torch.cuda.synchronize()
-        exec_mode = plan.info()["exec"]
-    err = relerrs(got.cpu().numpy(), ref)
     ranges = oracle.snapshot_ranges(g.r0, g.dr, g.steps, g.stride)
-    print(f"\nperiodic 200 Hz, FP32 (exec {exec_mode}), oracle {t_or:.1f} s; rel-L2 vs range:")
-    for r, e in zip(ranges, err):
-        print(f"  r = {r:8.1f} m  rel-L2 = {e:.3e}")
-    assert err.max() < TOL32, err
+    for exec_mode in (P.PE3D_EXEC_PERSISTENT, P.PE3D_EXEC_RESIDENT):
+        with P.Plan.for_grid(g, fp32=True, exec_mode=exec_mode) as plan:
+            plan.set_medium(torch.from_numpy(wl.n2).cuda(), wl.slice_r)
+            got = plan.march(torch.from_numpy(wl.u0.astype(np.complex64)).cuda(), g.r0, g.steps, g.stride)
+            torch.cuda.synchronize()
+            ran = plan.info()["exec"]
+        err = relerrs(got.cpu().numpy(), ref)
+        print(f"\nperiodic 200 Hz, FP32 (exec {ran}), oracle {t_or:.1f} s; rel-L2 vs range:")
+        for r, e in zip(ranges, err):
+            print(f"  r = {r:8.1f} m  rel-L2 = {e:.3e}")
+        assert err.max() < TOL32, err
 
 
 def test_config4_frequency_subset(P, oracle_lib):

@@ -106,7 +106,7 @@ def test_interp_in_batch(P, oracle_lib):
                          [1, 1], outs)
     torch.cuda.synchronize()
     for wl, it, out in zip(wls, interp, outs):
-        alone, _ = gpu_march(P, wl, fp32=True, interp=it)
+        alone, _ = gpu_march(P, wl, fp32=True, interp=it, exec_mode=3)
         assert np.array_equal(out.cpu().numpy(), alone)
         ref = oracle_lib.march(wl.grid, wl.n2, wl.slice_r, wl.u0, interp=it)
         assert relerrs(alone, ref).max() < TOL32

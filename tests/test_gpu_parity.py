@@ -179,9 +179,10 @@ def test_exec_modes_bitwise_equal(P, fp32):
 def test_resume_bitwise(P, fp32):
     """march(2N) equals march(N) followed by march(N) from the stored field."""
     wl = workloads.random_case(200, 40, periodic=False, K=3, steps=10, seed=78, stride=5)
-    full, _ = gpu_march(P, wl, fp32=fp32)
-    half, _ = gpu_march(P, wl, fp32=fp32, steps=5, stride=5)
-    rest, _ = gpu_march(P, wl, fp32=fp32, steps=5, stride=5, r0=wl.grid.r0 + 5 * wl.grid.dr, u0=half[-1])
+    full, _ = gpu_march(P, wl, fp32=fp32, exec_mode=3)
+    half, _ = gpu_march(P, wl, fp32=fp32, steps=5, stride=5, exec_mode=3)
+    rest, _ = gpu_march(P, wl, fp32=fp32, steps=5, stride=5, r0=wl.grid.r0 + 5 * wl.grid.dr, u0=half[-1],
+                        exec_mode=3)
     assert np.array_equal(full[-1], rest[-1])
 
 
@@ -266,6 +267,17 @@ def test_config2_fp32(P, config2):
     assert err.max() < 1e-4, err
 
 
+def test_config2_fp32_resident(P, config2):
+    """The same march in the resident launch (what AUTO picks for it), within
+    1e-4 of the oracle."""
+    wl, ref = config2
+    got, info = gpu_march(P, wl, fp32=True, exec_mode=4)
+    err = relerrs(got, ref)
+    print("config2 fp32 resident rel-L2 vs range:", np.array2string(err, precision=2))
+    assert info["exec"] == 4
+    assert err.max() < 1e-4, err
+
+
 # ---------------------------------------------------------------------------
 # batched multi-march
 # ---------------------------------------------------------------------------
@@ -294,7 +306,7 @@ def test_batched_matches_single_marches(P, oracle_lib):
             if st == 0:
                 continue
             got = out[:st].cpu().numpy()
-            alone, _ = gpu_march(P, wl, fp32=fp32)
+            alone, _ = gpu_march(P, wl, fp32=fp32, exec_mode=3)
             assert np.array_equal(got, alone)
             ref = oracle_lib.march(wl.grid, wl.n2, wl.slice_r, wl.u0)
             assert relerrs(got, ref).max() < (TOL32 if fp32 else TOL64)
@@ -387,7 +399,7 @@ def test_batch_of_more_than_64_marches(P):
     # two batched launches, a prologue per march, one azimuth set-up for all
     assert P.pe3d_plan_info(plans[0].h)["launches"] == 2 + len(wls) + 1
     for i in (0, 1, 63, 64, 69):
-        alone, _ = gpu_march(P, wls[i], fp32=True)
+        alone, _ = gpu_march(P, wls[i], fp32=True, exec_mode=3)
         assert np.array_equal(outs[i].cpu().numpy(), alone)
     for pl in plans:
         pl.close()

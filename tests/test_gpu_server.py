@@ -21,9 +21,12 @@ def P():
 
 
 def alone(P, wl, fp32):
+    """The same march alone, in the persistent launch: the request loop runs
+    the batched kernel, whose per-system arithmetic the persistent launch shares
+    (the resident launch rounds in another order)."""
     g = wl.grid
     cdt = np.complex64 if fp32 else np.complex128
-    with P.Plan.for_grid(g, fp32=fp32) as plan:
+    with P.Plan.for_grid(g, fp32=fp32, exec_mode=P.PE3D_EXEC_PERSISTENT) as plan:
         plan.set_medium(wl.n2, wl.slice_r)
         out = np.zeros((g.steps // g.stride, g.Ntheta, g.Nz), cdt)
         P.pe3d_march(plan.h, wl.u0.astype(cdt), g.r0, g.steps, g.stride, out)

@@ -37,27 +37,32 @@ CASES = [
 
 
 @pytest.mark.parametrize("case", CASES, ids=[f"{c[0]}x{c[1]}{'p' if c[2] else 'w'}" for c in CASES])
-@pytest.mark.parametrize("exec_mode", [1, 2], ids=["stream", "graph"])
+@pytest.mark.parametrize("exec_mode", [1, 2, 3], ids=["stream", "graph", "persistent"])
 @pytest.mark.parametrize("fp32", [False, True], ids=["fp64", "fp32"])
 def test_taylor_parity(P, oracle_lib, case, exec_mode, fp32):
     Nz, Nt, periodic, K, steps = case
     wl = workloads.random_case(Nz, Nt, periodic=periodic, K=K, steps=steps, seed=170 + Nz, stride=1)
     ref = oracle_lib.march(wl.grid, wl.n2, wl.slice_r, wl.u0, taylor=True)
     got, info = gpu_march(P, wl, fp32=fp32, exec_mode=exec_mode, scheme=P.PE3D_SCHEME_TAYLOR)
+    assert info["exec"] == exec_mode
     assert relerrs(got, ref).max() < (TOL32 if fp32 else TOL64)
     # a different scheme from Eq. 4
     assert relerrs(got, oracle_lib.march(wl.grid, wl.n2, wl.slice_r, wl.u0)).max() > 1e-6
+    if exec_mode == 3:   # the persistent launch runs the same per-system arithmetic as the per-step launches
+        stepwise, _ = gpu_march(P, wl, fp32=fp32, exec_mode=1, scheme=P.PE3D_SCHEME_TAYLOR)
+        assert np.array_equal(got, stepwise)
 
 
 @pytest.mark.parametrize("zthreads", [32, 64, 256])
 def test_taylor_layouts(P, oracle_lib, zthreads):
     """Other depth layouts (threads per system, hence chunk classes) and the
-    centred Y with the automatic launch (the stream launch for this scheme)."""
+    centred Y with the automatic launch (the persistent launch for this scheme
+    when its three-column depth unit fits)."""
     wl = workloads.random_case(700, 20, periodic=False, K=2, steps=5, seed=180, stride=5)
     for mid in (False, True):
         ref = oracle_lib.march(wl.grid, wl.n2, wl.slice_r, wl.u0, taylor=True, y_midpoint=mid)
         got, info = gpu_march(P, wl, fp32=True, zthreads=zthreads, scheme=P.PE3D_SCHEME_TAYLOR, y_midpoint=mid)
-        assert info["exec"] == 1                      # stream
+        assert info["exec"] == 3                      # persistent
         assert relerrs(got, ref).max() < TOL32
 
 
@@ -74,8 +79,8 @@ def test_taylor_refusals(P):
         with pytest.raises(P.PE3DError) as e:        # the scheme is fixed once a medium is set
             P.pe3d_set_option(plan.h, P.PE3D_OPT_SCHEME, P.PE3D_SCHEME_PADE)
         assert e.value.code == P.PE3D_ERR_STATE
-        P.pe3d_set_option(plan.h, P.PE3D_OPT_EXEC, 3)
-        with pytest.raises(P.PE3DError) as e:        # no persistent launch
+        P.pe3d_set_option(plan.h, P.PE3D_OPT_EXEC, 4)
+        with pytest.raises(P.PE3DError) as e:        # no resident launch
             plan.march(u0, wl.grid.r0, 2, 1)
         assert e.value.code == P.PE3D_ERR_ARG
         out = torch.zeros((2, 5, 20), dtype=torch.complex64, device="cuda")
