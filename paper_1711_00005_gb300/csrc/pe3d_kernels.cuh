@@ -340,10 +340,10 @@ __device__ bool computeA(const MarchArgs<C>& P, int base, unsigned char* smem, i
 template <typename C>
 __host__ __device__ inline size_t grpA3_bytes(int ldz) { return align128((size_t)3 * ldz * sizeof(C)); }
 
-// thread 0: the unit's columns of w and of both factors' multipliers
+// thread 0: the unit's columns of w and (with_mu) of both factors' multipliers
 template <typename C>
 __device__ __forceinline__ void loadA_taylor(const MarchArgs<C>& P, int slice, int base, unsigned char* smem,
-                                             uint32_t& par) {
+                                             uint32_t& par, bool with_mu = true) {
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem) + MB_A;
     par |= 1u << (INFLIGHT + MB_A);
     const int ldz = P.ldz;
@@ -353,12 +353,14 @@ __device__ __forceinline__ void loadA_taylor(const MarchArgs<C>& P, int slice, i
     const int nact = min(P.NG, P.Nt - base);
     const uint32_t colb = (uint32_t)(ldz * sizeof(C));
     fence_proxy_async_smem();
-    mbar_arrive_expect_tx(mbar, 3u * nact * colb);
+    mbar_arrive_expect_tx(mbar, (with_mu ? 3u : 1u) * nact * colb);
     for (int g = 0; g < nact; ++g) {
         C* dw = reinterpret_cast<C*>(smem + P.sp.a[0] + g * gstride);
         bulk_g2s(dw, P.w + (size_t)(base + g) * ldz, colb, mbar);
-        bulk_g2s(dw + ldz, m1 + (size_t)(base + g) * ldz, colb, mbar);
-        bulk_g2s(dw + 2 * ldz, m2 + (size_t)(base + g) * ldz, colb, mbar);
+        if (with_mu) {
+            bulk_g2s(dw + ldz, m1 + (size_t)(base + g) * ldz, colb, mbar);
+            bulk_g2s(dw + 2 * ldz, m2 + (size_t)(base + g) * ldz, colb, mbar);
+        }
     }
 }
 
@@ -916,7 +918,7 @@ __global__ void __launch_bounds__(NT) k_march_persistent(const __grid_constant__
     unsigned nb = 0;
     const int unitsA = (P.Nt + P.NG - 1) / P.NG;
     const bool hasA = bid < unitsA, hasB = bid < P.tiles;
-    const bool keepA = !TAYLOR && P.sp.keepA && unitsA <= G;     // one depth unit per CTA
+    const bool keepA = P.sp.keepA && unitsA <= G;     // one depth unit per CTA
     // thread 0 reads the next step's slice one step ahead
     int sl_next = (threadIdx.x == 0 && P.j0 < P.j1) ? P.slice_of_step[P.j0] : 0;
     int sl_held = -1;                                 // slice of the multipliers in a[0] (keepA)
@@ -927,7 +929,10 @@ __global__ void __launch_bounds__(NT) k_march_persistent(const __grid_constant__
         const int sl = sl_next;
         // phase A (Eq. 5)
         if constexpr (TAYLOR) {
-            if (hasA && threadIdx.x == 0) loadA_taylor(P, sl, bid * P.NG, smem, par);
+            if (hasA && threadIdx.x == 0) {   // both factors' multipliers stay while the slice does (keepA)
+                loadA_taylor(P, sl, bid * P.NG, smem, par, !(keepA && sl == sl_held));
+                sl_held = keepA ? sl : -1;
+            }
             if (threadIdx.x == 0 && j + 1 < P.j1) sl_next = P.slice_of_step[j + 1];
             for (int u = bid; u < unitsA; u += G) {
                 if (!computeA_taylor<C, LA>(P, u * P.NG, smem, par)) PE3D_ABORT();   // returns with the buffer free

@@ -291,8 +291,8 @@ SmemPlan single_unit_plan(const pe3d_plan_s* p) {
 // SM (or one per unit when there are fewer): units beyond the grid are
 // double-buffered when the buffers fit, and a CTA with a single depth unit
 // keeps its multipliers in shared memory.  The Taylor form's depth units
-// (three columns per system) take one buffer and keep nothing; sp->total = 0
-// when they do not fit.
+// (three columns per system) take one buffer, and keep both factors'
+// multipliers the same way; sp->total = 0 when they do not fit.
 template <typename C>
 void persistent_config_n(const pe3d_plan_s* p, int per, SmemPlan* sp, int* grid) {
     const int unitsA = (p->Nt + p->NG - 1) / p->NG;
@@ -302,7 +302,7 @@ void persistent_config_n(const pe3d_plan_s* p, int per, SmemPlan* sp, int* grid)
     if (p->scheme == PE3D_SCHEME_TAYLOR) {
         if (!plan_smem_sizes<C>((size_t)p->NG * grpA3_bytes<C>(p->ldz), tile_bytes<C>(p->rowsB, p->TZ),
                                 coef_bytes<C>(p->NtP, p->boundary == PE3D_PERIODIC), p->NG, p->TZ, false,
-                                p->tiles > G, false, true, budget, sp))
+                                p->tiles > G, unitsA <= G, true, budget, sp))
             sp->total = 0;
         return;
     }
