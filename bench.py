@@ -5,10 +5,10 @@ One bench step = one pass of the whole hot path over the medium-sized
 100 Hz workload (Nz=1067 x Ntheta=256, 2000 range steps, 101 medium slices):
 FP64 coefficient setup of every slice's depth systems (pe3d_set_medium from a
 device-resident n^2), then the march itself (per-step FP64 azimuth setup,
-then the complex-FP32 range steps in one cooperative launch: the resident
-march, or the persistent one where the autotuner finds it faster), all through the
-library's C ABI.  The metric is grid-point range-steps per second, at a
-relative L2 error against the FP64 oracle that the run measures and reports.
+then the complex-FP32 range steps in one persistent cooperative launch, in
+the layout the autotuner picks), all through the library's C ABI.  The
+metric is grid-point range-steps per second, at a relative L2 error against
+the FP64 oracle that the run measures and reports.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -239,7 +239,7 @@ WORKLOADS = {
     "medium-100Hz-interp": ("fp32", lambda: workloads.config2()),
     "medium-100Hz-taylor": ("fp32", lambda: workloads.config2()),
 }
-# workloads marched with the Taylor form of Eq. 3 (stream launches)
+# workloads marched with the Taylor form of Eq. 3
 TAYLOR_WORKLOADS = {"medium-100Hz-taylor"}
 # workloads whose n^2 is interpolated linearly in range, with the FP64 depth
 # systems set up for every range step
@@ -430,10 +430,18 @@ def run_ours(args):
     P.pe3d_set_medium(plan, n2_h, wl.slice_r)
     P.pe3d_march(plan, u0_h, g.r0, g.steps, g.stride, out_h)
     barrier()
+    t_sm = t_m = 0.0
+    e2e_each = []
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
+        ta = time.perf_counter()
         P.pe3d_set_medium(plan, n2_h, wl.slice_r)
+        tb = time.perf_counter()
         P.pe3d_march(plan, u0_h, g.r0, g.steps, g.stride, out_h)
+        tc = time.perf_counter()
+        t_sm += tb - ta
+        t_m += tc - tb
+        e2e_each.append(tc - ta)
     t_e2e = reduce_max((time.perf_counter() - t0) / e2e_steps, dev)
 
     # plain FP64 GPU march of the same workload, for comparison
@@ -528,9 +536,13 @@ def run_ours(args):
             "max_rel_l2_vs_oracle": err,
             "roofline": roof,
             "cpu_baseline": cpu,
-            "e2e": {"value": total_units / args.steps / t_e2e * (1 if world == 1 else 1), "unit": UNIT,
+            "e2e": {"value": total_units / args.steps / t_e2e, "unit": UNIT,
                     "h2d_bytes_per_step": int(wl.n2.nbytes + wl.u0.astype(cdt).nbytes),
-                    "d2h_bytes_per_step": int(out_h.numel() * out_h.element_size())},
+                    "d2h_bytes_per_step": int(out_h.numel() * out_h.element_size()),
+                    "ms_per_step": t_e2e * 1e3,
+                    "ms_min_median_max": [round(1e3 * min(e2e_each), 3), round(1e3 * statistics.median(e2e_each), 3),
+                                          round(1e3 * max(e2e_each), 3)],
+                    "set_medium_ms": t_sm / e2e_steps * 1e3, "march_ms": t_m / e2e_steps * 1e3},
             "gpu_launches": int(launches),
             "clocks": clocks,
         }
@@ -905,7 +917,7 @@ def run_served(args):
         "server_stats": stats, "wall_s": wall, "clocks": clocks,
         "roofline": None, "cpu_baseline": None,
         "e2e": {"value": value, "unit": UNIT, "note": "host media in, host fields out through pe3d_submit/poll"},
-        "gpu_launches": None,
+        "gpu_launches": stats.get("launches"),
     }
     print(json.dumps(line), flush=True)
     return 0

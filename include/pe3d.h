@@ -334,7 +334,9 @@ int pe3d_poll(pe3d_server_t srv, uint64_t id, int *state, void *out, double *tim
 int pe3d_server_destroy(pe3d_server_t srv);
 
 /* Server counters: [0] submitted, [1] admitted, [2] finished, [3] failed,
- * [4] ticks, [5] grid-point range-steps done, [6] device bytes in use. */
+ * [4] ticks, [5] grid-point range-steps done, [6] device bytes in use,
+ * [7] kernels launched (the requests' set-up and the batched turns).  Writes
+ * min(n, 8) counters and returns that count. */
 int pe3d_server_stats(pe3d_server_t srv, int64_t *stats, int n);
 
 #ifdef __cplusplus

@@ -323,9 +323,9 @@ def pe3d_server_destroy(server) -> None:
 
 
 def pe3d_server_stats(server) -> dict:
-    buf = (ctypes.c_int64 * 7)()
-    n = _check(load_library().pe3d_server_stats(server, buf, 7))
-    keys = ("submitted", "admitted", "finished", "failed", "ticks", "point_steps", "device_bytes")
+    keys = ("submitted", "admitted", "finished", "failed", "ticks", "point_steps", "device_bytes", "launches")
+    buf = (ctypes.c_int64 * len(keys))()
+    n = _check(load_library().pe3d_server_stats(server, buf, len(keys)))
     return {keys[i]: int(buf[i]) for i in range(n)}
 
 

@@ -788,71 +788,112 @@ __device__ __forceinline__ bool grid_barrier(unsigned* ctr, unsigned target, int
 template <typename C>
 __device__ __forceinline__ double2 ld64(const C* p) { return to64(__ldcg(p)); }
 
-// [1 + f (d/4) Y] u at (m, l) in FP64, f = +1 (B') or -1 (B)
-template <typename C>
-__device__ double2 theta_apply64(const MarchArgs<C>& P, const C* u, int m, int l, double2 yq) {
-    const int Nt = P.Nt;
-    const size_t ld = P.ldz;
-    const double2 c = ld64(u + (size_t)m * ld + l);
-    double2 up = make_double2(0.0, 0.0), dn = make_double2(0.0, 0.0);
-    if (m + 1 < Nt) up = ld64(u + (size_t)(m + 1) * ld + l); else if (P.periodic) up = ld64(u + l);
-    if (m > 0) dn = ld64(u + (size_t)(m - 1) * ld + l); else if (P.periodic) dn = ld64(u + (size_t)(Nt - 1) * ld + l);
-    const double2 lap = make_double2(up.x + dn.x - 2.0 * c.x, up.y + dn.y - 2.0 * c.y);
-    return cadd(c, cmul(yq, lap));
+// Work of the residual and combine phases: warps take strips of consecutive
+// depths (coalesced rows) and walk a run of azimuths, holding each row's
+// azimuth neighbours in registers, so every point of u^j, u~ and d is loaded
+// once per row it feeds.  The split of (strip, azimuth run) items over the
+// grid depends on the grid, but every point's arithmetic does not.
+struct RowWalk {
+    int nstrip, mlen, items, wid, nwarp;
+    __device__ RowWalk(int width, int Nt, int strip) {
+        nstrip = (width + strip - 1) / strip;
+        nwarp = gridDim.x * (NT / 32);
+        wid = blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
+        const int mb = min(Nt, max(1, nwarp / nstrip));
+        mlen = (Nt + mb - 1) / mb;
+        items = nstrip * ((Nt + mlen - 1) / mlen);
+    }
+};
+// the azimuth neighbour of row m in direction +1 / -1, or -1 past a wall
+__device__ __forceinline__ int row_next(int m, int Nt, bool periodic) {
+    return m + 1 < Nt ? m + 1 : (periodic ? 0 : -1);
+}
+__device__ __forceinline__ int row_prev(int m, int Nt, bool periodic) {
+    return m > 0 ? m - 1 : (periodic ? Nt - 1 : -1);
 }
 
+// Outputs per warp row of the residual: lanes 1..30 hold depths l0..l0+29,
+// lanes 0 and 31 their depth neighbours l0-1 and l0+30.
+constexpr int RC_STRIP = 30;
+
+// Since X is linear,
+//   r = [1 + beta X] a - [1 + alpha X] b = (a - b) + X (beta a - alpha b),
+// a = [1 + (d/4) Y] u^j, b = [1 - (d/4) Y] u~; beta = 1/4 + i kd/4 and
+// alpha = 1/4 - i kd/4 give beta a - alpha b = (a - b)/4 + i (kd/4)(a + b).
+// X g = (n^2 - 1) g + s (g_{l+1} + g_{l-1} - 2 g_l) with zero ghosts (g = 0
+// outside 0 <= l < Nz); Y's stencil has zero ghosts past a wall and wraps
+// for a full circle.  r = 0 on the depth padding.  Every operation is an
+// explicit rounded sum, product or FMA, so the persistent march and the
+// batched correction, which inline this in different code, round alike.
 template <typename C>
 __device__ void residual_phase(const MarchArgs<C>& P, int j) {
-    const double kd = P.k0 * P.dr;
-    const double s = 1.0 / ((P.k0 * P.dz) * (P.k0 * P.dz));
-    const double rs = P.r0 + ((double)(j + 1) - (P.y_mid ? 0.5 : 0.0)) * P.dr;   // where Y is evaluated
-    const double c = 1.0 / ((P.k0 * rs * P.dtheta) * (P.k0 * rs * P.dtheta));
-    const double2 yq = make_double2(0.0, kd * c / 4.0);          // (d/4) c
-    const double2 myq = make_double2(0.0, -kd * c / 4.0);
-    const double2 alpha = make_double2(0.25, -kd / 4.0);
-    const double2 beta = make_double2(0.25, kd / 4.0);
+    const double kd = __dmul_rn(P.k0, P.dr);
+    const double kdz = __dmul_rn(P.k0, P.dz);
+    const double s = 1.0 / __dmul_rn(kdz, kdz);
+    const double rs = __dadd_rn(P.r0, __dmul_rn(__dsub_rn((double)(j + 1), P.y_mid ? 0.5 : 0.0), P.dr));
+    const double krt = __dmul_rn(__dmul_rn(P.k0, rs), P.dtheta);
+    const double c = 1.0 / __dmul_rn(krt, krt);                  // where Y is evaluated
+    const double yc = __dmul_rn(__dmul_rn(kd, c), 0.25);         // (d/4) c = i yc
+    const double bq = __dmul_rn(kd, 0.25);
     const size_t sl = (size_t)P.Nt * P.Nz;
     const double2* n2 = P.n2 + (P.lerp ? (size_t)P.lerp[j].k : (size_t)P.slice_of_step[j]) * sl;
     const double2* n2b = P.lerp ? P.n2 + (size_t)P.lerp[j].k1 * sl : n2;
     const double tl = P.lerp ? P.lerp[j].t : 0.0;
-    const long long n = (long long)P.Nt * P.ldz;
-    for (long long idx = (long long)blockIdx.x * NT + threadIdx.x; idx < n; idx += (long long)gridDim.x * NT) {
-        const int m = (int)(idx / P.ldz), l = (int)(idx - (long long)m * P.ldz);
-        double2 r = make_double2(0.0, 0.0);
-        if (l < P.Nz) {
-            double2 t1[3], t2[3];
-#pragma unroll
-            for (int d = -1; d <= 1; ++d) {
-                const int ll = l + d;
-                if (ll >= 0 && ll < P.Nz) {
-                    t1[d + 1] = theta_apply64(P, P.up, m, ll, yq);
-                    t2[d + 1] = theta_apply64(P, P.ut, m, ll, myq);
-                } else {
-                    t1[d + 1] = make_double2(0.0, 0.0);
-                    t2[d + 1] = make_double2(0.0, 0.0);
+    const int Nt = P.Nt, Nz = P.Nz, ldz = P.ldz;
+    const size_t ld = P.ldz;
+    const int lane = threadIdx.x & 31;
+    const double2 zero = make_double2(0.0, 0.0);
+    // u + v - 2 w, component-wise
+    auto lap = [](double2 u, double2 v, double2 w) {
+        return make_double2(__fma_rn(-2.0, w.x, __dadd_rn(u.x, v.x)), __fma_rn(-2.0, w.y, __dadd_rn(u.y, v.y)));
+    };
+    const RowWalk W(ldz, Nt, RC_STRIP);
+    for (int it = W.wid; it < W.items; it += W.nwarp) {             // warp-uniform
+        const int strip = it % W.nstrip, m0 = (it / W.nstrip) * W.mlen, m1 = min(Nt, m0 + W.mlen);
+        const int l = strip * RC_STRIP - 1 + lane;
+        const bool in = l >= 0 && l < Nz;
+        const bool out = lane >= 1 && lane <= RC_STRIP && l < ldz;
+        auto row = [&](const C* u, int m) { return (in && m >= 0) ? ld64(u + (size_t)m * ld + l) : zero; };
+        const int mp = row_prev(m0, Nt, P.periodic);
+        double2 pd = row(P.up, mp), td = row(P.ut, mp);
+        double2 pc = row(P.up, m0), tc = row(P.ut, m0);
+        for (int m = m0; m < m1; ++m) {
+            const int mn = row_next(m, Nt, P.periodic);
+            const double2 pu = row(P.up, mn), tu = row(P.ut, mn);
+            const double2 lp = lap(pu, pd, pc), lt = lap(tu, td, tc);
+            const double2 a = make_double2(__fma_rn(-yc, lp.y, pc.x), __fma_rn(yc, lp.x, pc.y));
+            const double2 b = make_double2(__fma_rn(yc, lt.y, tc.x), __fma_rn(-yc, lt.x, tc.y));
+            const double2 dmb = make_double2(__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y));
+            const double2 g = make_double2(__fma_rn(0.25, dmb.x, __dmul_rn(-bq, __dadd_rn(a.y, b.y))),
+                                           __fma_rn(0.25, dmb.y, __dmul_rn(bq, __dadd_rn(a.x, b.x))));
+            const double2 gm = make_double2(__shfl_up_sync(0xffffffffu, g.x, 1), __shfl_up_sync(0xffffffffu, g.y, 1));
+            const double2 gp = make_double2(__shfl_down_sync(0xffffffffu, g.x, 1),
+                                            __shfl_down_sync(0xffffffffu, g.y, 1));
+            if (out) {
+                double2 r = zero;
+                if (l < Nz) {
+                    double2 q = n2[(size_t)m * Nz + l];
+                    if (P.lerp) q = medium_lerp(q, n2b[(size_t)m * Nz + l], tl);
+                    q.x = __dsub_rn(q.x, 1.0);
+                    const double2 qg = cmul(q, g), zg = lap(gp, gm, g);
+                    r = make_double2(__dadd_rn(dmb.x, __fma_rn(s, zg.x, qg.x)),
+                                     __dadd_rn(dmb.y, __fma_rn(s, zg.y, qg.y)));
                 }
+                __stcg(P.v + (size_t)m * ld + l, from64<C>(r));
             }
-            double2 q = n2[(size_t)m * P.Nz + l];
-            if (P.lerp) q = medium_lerp(q, n2b[(size_t)m * P.Nz + l], tl);
-            q.x -= 1.0;
-            const double2 x1 = cadd(cmul(q, t1[1]),
-                                    make_double2(s * (t1[2].x + t1[0].x - 2.0 * t1[1].x),
-                                                 s * (t1[2].y + t1[0].y - 2.0 * t1[1].y)));
-            const double2 x2 = cadd(cmul(q, t2[1]),
-                                    make_double2(s * (t2[2].x + t2[0].x - 2.0 * t2[1].x),
-                                                 s * (t2[2].y + t2[0].y - 2.0 * t2[1].y)));
-            r = csub(cadd(t1[1], cmul(beta, x1)), cadd(t2[1], cmul(alpha, x2)));
+            pd = pc; pc = pu;
+            td = tc; tc = tu;
         }
-        __stcg(P.v + idx, from64<C>(r));
     }
 }
 
 // u^{j+1} = u~ + d (FP64 add), then the next step's azimuth stencil, the
-// snapshot and, when the next step is corrected too, up
+// snapshot and, when the next step is corrected too, up.  Warps walk rows of
+// 32 depths along the azimuth, so each corrected value is formed once.
 template <typename C>
 __device__ void combine_phase(const MarchArgs<C>& P, int j) {
     using R = typename real_of<C>::type;
-    const int Nt = P.Nt;
+    const int Nt = P.Nt, Nz = P.Nz, ldz = P.ldz;
     const size_t ld = P.ldz;
     const C q = from64<C>(P.sc[j].qnext);
     const bool snap = P.snap != nullptr && ((j + 1) % P.stride) == 0;
@@ -860,24 +901,32 @@ __device__ void combine_phase(const MarchArgs<C>& P, int j) {
     const C hk = snap && P.out_mode != OUT_FIELD ? step_hankel(P.sc + j, C{}) : czero<C>();
     const bool keep = P.rc_every > 0 && (j + 2) % P.rc_every == 0;
     const C two = cmake((R)2, (R)0);
-    const long long n = (long long)Nt * ld;
-    for (long long idx = (long long)blockIdx.x * NT + threadIdx.x; idx < n; idx += (long long)gridDim.x * NT) {
-        const int m = (int)(idx / ld), l = (int)(idx - (long long)m * ld);
+    const int lane = threadIdx.x & 31;
+    const RowWalk W(ldz, Nt, 32);
+    for (int it = W.wid; it < W.items; it += W.nwarp) {
+        const int strip = it % W.nstrip, m0 = (it / W.nstrip) * W.mlen, m1 = min(Nt, m0 + W.mlen);
+        const int l = strip * 32 + lane;
+        const bool in = l < Nz;
+        if (l >= ldz) continue;
         auto corrected = [&](int mm) -> C {
+            if (!in || mm < 0) return czero<C>();
             const size_t o = (size_t)mm * ld + l;
             return from64<C>(cadd(ld64(P.ut + o), ld64(P.db + o)));
         };
-        C w = czero<C>(), u = czero<C>();
-        if (l < P.Nz) {
-            u = corrected(m);
-            C upv = czero<C>(), dnv = czero<C>();
-            if (m + 1 < Nt) upv = corrected(m + 1); else if (P.periodic) upv = corrected(0);
-            if (m > 0) dnv = corrected(m - 1); else if (P.periodic) dnv = corrected(Nt - 1);
-            w = cfma(q, csub(cadd(upv, dnv), cmul(two, u)), u);
-            if (snap) store_snapshot(P.snap, sp + (size_t)m * P.snap_ld + l, u, P.out_mode, hk);
-            if (keep) __stcg(P.up + idx, u);
+        C dnv = corrected(row_prev(m0, Nt, P.periodic));
+        C u = corrected(m0);
+        for (int m = m0; m < m1; ++m) {
+            const C upv = corrected(row_next(m, Nt, P.periodic));
+            C w = czero<C>();
+            if (in) {
+                w = cfma(q, csub(cadd(upv, dnv), cmul(two, u)), u);
+                if (snap) store_snapshot(P.snap, sp + (size_t)m * P.snap_ld + l, u, P.out_mode, hk);
+                if (keep) __stcg(P.up + (size_t)m * ld + l, u);
+            }
+            __stcg(P.w + (size_t)m * ld + l, w);
+            dnv = u;
+            u = upv;
         }
-        __stcg(P.w + idx, w);
     }
 }
 
@@ -1215,6 +1264,16 @@ __device__ __forceinline__ bool pivot_ok(double nrm) {
     return hi - lo < top - lo;
 }
 
+// One pivot: mu_l from b_l = d_l / e and mu_{l-1}; clears ok if the pivot
+// leaves the range pivot_ok admits.
+__device__ __forceinline__ double2 pivot_step(double2 b, double2 mprev, bool& ok) {
+    const double2 den = make_double2(b.x + mprev.x, b.y + mprev.y);
+    const double nrm = fma(den.x, den.x, den.y * den.y);
+    ok &= pivot_ok(nrm);
+    const double inv = recip_newton(nrm);
+    return make_double2(-den.x * inv, den.y * inv);
+}
+
 // Depth systems: row l of A = I + alpha X has diagonal
 // d_l = 1 + alpha (n^2_l - 1 - 2 s) and constant off-diagonal e = alpha s; with
 // pivots p_l = d_l - e^2 / p_{l-1} the stored multiplier is
@@ -1226,12 +1285,7 @@ __device__ __forceinline__ bool depth_pivots(B b_at, int Nz, int ldz, C* __restr
     double2 mprev = make_double2(0.0, 0.0);
     bool ok = true;
     for (int l = 0; l < Nz; ++l) {
-        const double2 b = b_at(l);
-        const double2 den = make_double2(b.x + mprev.x, b.y + mprev.y);
-        const double nrm = fma(den.x, den.x, den.y * den.y);
-        ok &= pivot_ok(nrm);
-        const double inv = recip_newton(nrm);
-        const double2 mu = make_double2(-den.x * inv, den.y * inv);
+        const double2 mu = pivot_step(b_at(l), mprev, ok);
         out[l] = from64<C>(mu);
         mprev = mu;
     }

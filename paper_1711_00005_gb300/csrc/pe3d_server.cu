@@ -93,6 +93,8 @@ struct pe3d_server_s {
     size_t used = 0;
     std::chrono::steady_clock::time_point t0;
     int64_t n_submitted = 0, n_admitted = 0, n_finished = 0, n_failed = 0, n_ticks = 0, point_steps = 0;
+    int64_t setup_launches = 0;           // kernels the admission thread launched (set-up of each request)
+    int64_t tick_launches = 0;            // kernels of the batched turns (the owner plan's count)
 
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -161,6 +163,10 @@ bool pe3d_server_s::start(Request* q) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
         if (e != cudaSuccess) rc = cuda_fail(e, "request set-up");
         else if (st) rc = fail(st, "singular system in the request's azimuth set-up");
+    }
+    if (q->plan) {
+        std::lock_guard<std::mutex> lk(mu);
+        setup_launches += q->plan->total_launches;
     }
     if (rc) {
         finish(q, false, pe3d_last_error());
@@ -252,6 +258,7 @@ bool pe3d_server_s::tick() {
     {
         std::lock_guard<std::mutex> lk(mu);
         ++n_ticks;
+        tick_launches = owner->total_launches;
     }
     std::vector<Request*> done;
     for (Request* q : act) {
@@ -425,8 +432,8 @@ int pe3d_server_stats(pe3d_server_t s, int64_t* stats, int n) {
     if (!s || !stats || n < 0) return fail(PE3D_ERR_ARG, "bad argument");
     std::lock_guard<std::mutex> lk(s->mu);
     const int64_t v[] = {s->n_submitted, s->n_admitted, s->n_finished, s->n_failed, s->n_ticks, s->point_steps,
-                         (int64_t)s->used};
-    const int cnt = std::min<int>(n, 7);
+                         (int64_t)s->used, s->setup_launches + s->tick_launches};
+    const int cnt = std::min<int>(n, 8);
     for (int i = 0; i < cnt; ++i) stats[i] = v[i];
     return cnt;
 }

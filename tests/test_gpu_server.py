@@ -71,6 +71,8 @@ def test_alone_equals_mix(P, oracle_lib):
              for i, (Nz, Nt, per, st, fp32) in enumerate(specs)]
     outs, times, stats = serve(P, items, stagger=0.003)
     assert stats["finished"] == len(items) and stats["failed"] == 0
+    # every turn launches the batched march, every request its own set-up
+    assert stats["launches"] >= stats["ticks"] + len(items)
     for (wl, fp32), got in zip(items, outs):
         ref = alone(P, wl, fp32)
         assert np.array_equal(got, ref)          # same arithmetic alone and in the mix
