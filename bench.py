@@ -915,6 +915,7 @@ def run_served(args):
         "latency_s": {"p50": pct(0.50), "p99": pct(0.99), "max": lat[-1] if lat else None},
         "alone_vs_mix_bitwise": same, "alone_vs_mix_checked": len(sample),
         "server_stats": stats, "wall_s": wall, "clocks": clocks,
+        "gpu_busy_frac": (stats.get("kernel_us", 0) / 1e6 / wall) if wall > 0 else None,
         "roofline": None, "cpu_baseline": None,
         "e2e": {"value": value, "unit": UNIT, "note": "host media in, host fields out through pe3d_submit/poll"},
         "gpu_launches": stats.get("launches"),

@@ -27,7 +27,9 @@
  *  - "on_device" flags say whether a pointer is device memory of the plan's
  *    GPU (nonzero) or host memory (zero).  The library copies every input:
  *    callers keep ownership of their buffers.  The library owns all plan
- *    memory (device allocations made at pe3d_plan / pe3d_set_medium).
+ *    memory: device allocations made at pe3d_plan / pe3d_set_medium /
+ *    pe3d_march, stream-ordered on the plan's stream (cudaMallocAsync from
+ *    the device's default memory pool), so they wait for no other stream.
  *  - Work is ordered on the CUDA stream given to pe3d_plan.  A call whose
  *    output is host memory returns after the stream has finished it; a call
  *    whose inputs and outputs are all device memory returns once the work is
@@ -335,8 +337,10 @@ int pe3d_server_destroy(pe3d_server_t srv);
 
 /* Server counters: [0] submitted, [1] admitted, [2] finished, [3] failed,
  * [4] ticks, [5] grid-point range-steps done, [6] device bytes in use,
- * [7] kernels launched (the requests' set-up and the batched turns).  Writes
- * min(n, 8) counters and returns that count. */
+ * [7] kernels launched (the requests' set-up and the batched turns), [8] microseconds
+ * the scheduler spent in turns (launches, waits, retiring finished requests),
+ * [9] microseconds of GPU time of the turns' launches (CUDA events on the server's
+ * stream).  Writes min(n, 10) counters and returns that count. */
 int pe3d_server_stats(pe3d_server_t srv, int64_t *stats, int n);
 
 #ifdef __cplusplus

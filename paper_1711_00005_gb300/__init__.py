@@ -323,7 +323,8 @@ def pe3d_server_destroy(server) -> None:
 
 
 def pe3d_server_stats(server) -> dict:
-    keys = ("submitted", "admitted", "finished", "failed", "ticks", "point_steps", "device_bytes", "launches")
+    keys = ("submitted", "admitted", "finished", "failed", "ticks", "point_steps", "device_bytes", "launches",
+            "tick_us", "kernel_us")
     buf = (ctypes.c_int64 * len(keys))()
     n = _check(load_library().pe3d_server_stats(server, buf, len(keys)))
     return {keys[i]: int(buf[i]) for i in range(n)}

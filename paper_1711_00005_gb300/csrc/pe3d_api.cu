@@ -26,14 +26,21 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 size_t elem_bytes(const pe3d_plan_s* p) { return p->precision == PE3D_FP32 ? 8 : 16; }
 
+// Plan memory is stream-ordered on the plan's stream (the device's default
+// memory pool): unlike cudaMalloc / cudaFree, neither call waits for other
+// streams' work, so one plan's set-up or teardown (a request joining or
+// leaving the request loop) does not stall kernels running on other streams.
+// A buffer is used on another stream only after its plan's stream has been
+// synchronised (pe3d_set_medium and the request set-up end that way).
 int dev_alloc(pe3d_plan_s* p, void** ptr, size_t bytes) {
     *ptr = nullptr;
     if (bytes == 0) return PE3D_OK;
-    cudaError_t e = cudaMalloc(ptr, bytes);
+    cudaError_t e = cudaMallocAsync(ptr, bytes, p->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *ptr = nullptr;
-        return fail(PE3D_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+        return fail(PE3D_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed: " +
+                                      cudaGetErrorString(e));
     }
     p->bytes += (int64_t)bytes;
     return PE3D_OK;
@@ -41,7 +48,7 @@ int dev_alloc(pe3d_plan_s* p, void** ptr, size_t bytes) {
 
 void dev_free(pe3d_plan_s* p, void** ptr, size_t bytes) {
     if (*ptr) {
-        cudaFree(*ptr);
+        cudaFreeAsync(*ptr, p->stream);
         p->bytes -= (int64_t)bytes;
     }
     *ptr = nullptr;
@@ -118,9 +125,13 @@ static std::mutex g_prep_mu;
 static std::set<std::pair<const void*, void*>> g_prepared;
 
 bool context_prepared(const void* table) {
-    cudaFree(nullptr);   // make sure the current device's context exists
-    cudaGetLastError();
-    const std::pair<const void*, void*> key(table, current_context());
+    void* ctx = current_context();
+    if (!ctx) {   // bind (creating it on first use) the current device's primary context
+        cudaFree(nullptr);
+        cudaGetLastError();
+        ctx = current_context();
+    }
+    const std::pair<const void*, void*> key(table, ctx);
     std::lock_guard<std::mutex> lk(g_prep_mu);
     return key.second != nullptr && g_prepared.count(key) != 0;
 }
@@ -338,7 +349,14 @@ int pe3d_get_option(pe3d_plan_t p, int option, int* value) {
 }
 
 // Check and upload one plan's medium (no coefficient set-up yet)
-static int upload_medium(pe3d_plan_s* p, const void* n2, const double* slice_r, int K, int n2_on_device) {
+// Validate and size the medium buffers.  With `defer`, a medium in this
+// GPU's memory is not copied here: the depth set-up kernel reads it in place
+// and writes the plan's copy as it goes (one pass instead of a copy and a
+// pass).  A host medium is copied here: read in place across NVLink-C2C, the
+// set-up's per-system rows (16-byte reads, thread by thread) were slower
+// than a bulk copy followed by the set-up.
+static int upload_medium(pe3d_plan_s* p, const void* n2, const double* slice_r, int K, int n2_on_device,
+                         bool defer) {
     if (!p || !n2 || !slice_r) return fail(PE3D_ERR_ARG, "NULL argument");
     if (K < 1) return fail(PE3D_ERR_ARG, "K must be >= 1");
     for (int k = 0; k < K; ++k) {
@@ -363,8 +381,21 @@ static int upload_medium(pe3d_plan_s* p, const void* n2, const double* slice_r, 
         if ((rc = dev_alloc(p, &p->mz, mb))) return rc;
         p->mz_bytes = mb;
     }
-    PE3D_CUDA(cudaMemcpyAsync(p->n2, n2, nb, n2_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                              p->stream));
+    p->n2_src = nullptr;
+    p->n2_caller = n2;
+    p->n2_caller_on_device = n2_on_device != 0;
+    if (defer && n2_on_device) {   // read in place: memory of this GPU
+        cudaPointerAttributes a;
+        int dev = -1;
+        if (cudaPointerGetAttributes(&a, n2) == cudaSuccess && cudaGetDevice(&dev) == cudaSuccess) {
+            if ((a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev) p->n2_src = n2;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    if (!p->n2_src)
+        PE3D_CUDA(cudaMemcpyAsync(p->n2, n2, nb, n2_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  p->stream));
     p->nslices = K;
     p->slice_r.assign(slice_r, slice_r + K);
     return PE3D_OK;
@@ -372,9 +403,11 @@ static int upload_medium(pe3d_plan_s* p, const void* n2, const double* slice_r, 
 
 int pe3d_set_medium(pe3d_plan_t p, const void* n2, const double* slice_r, int K, int n2_on_device) {
     g_err.clear();
-    int rc = upload_medium(p, n2, slice_r, K, n2_on_device);
+    int rc = upload_medium(p, n2, slice_r, K, n2_on_device, true);
+    if (!rc) rc = slice_setup(p);
+    p->n2_src = nullptr;   // the caller's buffer is not read after this call
+    p->n2_caller = nullptr;
     if (rc) return rc;
-    if ((rc = slice_setup(p))) return rc;
     p->medium_ready = true;
     return PE3D_OK;
 }
@@ -393,7 +426,7 @@ int pe3d_set_medium_batched(int n, const pe3d_plan_t* plans, const void* const* 
     for (int i = 0; i < n; ++i) plans[i]->medium_ready = false;
     int rc;
     for (int i = 0; i < n; ++i)
-        if ((rc = upload_medium(plans[i], n2[i], slice_r[i], K[i], n2_on_device))) return rc;
+        if ((rc = upload_medium(plans[i], n2[i], slice_r[i], K[i], n2_on_device, false))) return rc;
     // one depth set-up launch for the piecewise Eq. 4 media; the others set up on their own
     std::vector<pe3d_plan_s*> flat;
     for (int i = 0; i < n; ++i) {
@@ -517,7 +550,8 @@ int pe3d_destroy(pe3d_plan_t p) {
                      &p->gscr, &p->sc, (void**)&p->slice_of_step, &p->lerp, &p->mzs, &p->dd, &p->setupbuf, &p->res_buf, (void**)&p->status,
                      (void**)&p->bar};
     for (void** b : bufs)
-        if (*b) { cudaFree(*b); *b = nullptr; }
+        if (*b) { cudaFreeAsync(*b, p->stream); *b = nullptr; }
+    cudaStreamSynchronize(p->stream);   // the memory is back in the pool (and released) on return
     delete p;
     return PE3D_OK;
 }
@@ -548,7 +582,7 @@ static void drop_layout(pe3d_plan_s* p) {
     p->mzs_bytes = 0;
     void** bufs[6] = {&p->mB, &p->zsm, &p->gscr, &p->sc, (void**)&p->slice_of_step, &p->lerp};
     for (int i = 0; i < 6; ++i) {   // per-step tables depend on NtP
-        if (*bufs[i]) { cudaFree(*bufs[i]); *bufs[i] = nullptr; }
+        if (*bufs[i]) { cudaFreeAsync(*bufs[i], p->stream); *bufs[i] = nullptr; }
     }
     p->step_cap = 0;
     p->ldz = 0;

@@ -57,6 +57,12 @@ struct pe3d_plan_s {
     size_t outstage_bytes = 0;
     void* n2 = nullptr;               // complex128 [nslices][Nt][Nz]
     size_t n2_bytes = 0;
+    // During pe3d_set_medium only: the caller's n^2 in this GPU's memory; the
+    // depth set-up reads it and writes the plan's copy n2 as it goes.
+    // nullptr when n2 already holds the medium.
+    const void* n2_src = nullptr;
+    const void* n2_caller = nullptr;  // the caller's pointer (host or device)
+    bool n2_caller_on_device = false;
     int nslices = 0;
     std::vector<double> slice_r;
     void* mz = nullptr;               // [nslices][Nt][ldz]

@@ -1316,13 +1316,26 @@ __device__ __forceinline__ void depth_system(const double2* __restrict__ row, in
     if (!depth_pivots<C>([row, doe](int l) { return doe(row[l]); }, Nz, ldz, out)) atomicExch(status, ST_SINGULAR);
 }
 
-// Depth systems of every slice: thread per (slice, azimuth).
+// Depth systems of every slice: thread per (slice, azimuth).  n2 may be the
+// caller's medium read in place; copy, if not null, receives it as it is read.
 template <typename C>
-__global__ void k_setupA(const double2* __restrict__ n2, int KNt, int Nz, int ldz, double2 alpha,
-                         double s, double2 einv, C* __restrict__ mz, int* status) {
+__global__ void k_setupA(const double2* __restrict__ n2, double2* __restrict__ copy, int KNt, int Nz, int ldz,
+                         double2 alpha, double s, double2 einv, C* __restrict__ mz, int* status) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= KNt) return;
-    depth_system<C>(n2 + (size_t)idx * Nz, Nz, ldz, alpha, s, einv, mz + (size_t)idx * ldz, status);
+    const double2* row = n2 + (size_t)idx * Nz;
+    if (copy) {
+        double2* crow = copy + (size_t)idx * Nz;
+        const DiagOverE doe(alpha, s, einv);
+        auto b_at = [row, crow, doe](int l) {
+            const double2 q = row[l];
+            crow[l] = q;
+            return doe(q);
+        };
+        if (!depth_pivots<C>(b_at, Nz, ldz, mz + (size_t)idx * ldz)) atomicExch(status, ST_SINGULAR);
+    } else {
+        depth_system<C>(row, Nz, ldz, alpha, s, einv, mz + (size_t)idx * ldz, status);
+    }
 }
 
 // Per-plan arguments of the multi-plan set-up kernels

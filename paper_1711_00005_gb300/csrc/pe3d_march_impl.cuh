@@ -162,6 +162,10 @@ int setupA(pe3d_plan_s* p) {
             if (rc) return rc;
             p->dd_bytes = b;
         }
+        if (p->n2_src)   // the slopes read the plan's copy
+            PE3D_CUDA(cudaMemcpyAsync(p->n2, p->n2_caller, p->n2_bytes,
+                                      p->n2_caller_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                      p->stream));
         const long long n = (long long)p->nslices * pts;
         const int grid = (int)std::min<long long>((n + 255) / 256, 16LL * p->num_sms);
         k_setupA_slopes<C><<<grid, 256, 0, p->stream>>>(reinterpret_cast<const double2*>(p->n2), p->nslices, pts,
@@ -171,22 +175,25 @@ int setupA(pe3d_plan_s* p) {
         return PE3D_OK;
     }
     const int KNt = p->nslices * p->Nt;
+    // the first launch reads the caller's medium in place where it can and
+    // writes the plan's copy; later launches read the copy
+    const double2* src = reinterpret_cast<const double2*>(p->n2_src ? p->n2_src : p->n2);
+    double2* copy = p->n2_src ? reinterpret_cast<double2*>(p->n2) : nullptr;
     if (p->scheme == PE3D_SCHEME_TAYLOR) {
         // the two tridiagonal factors I + a_k X of the Taylor form, slices of
         // factor 1 then of factor 2
         const TaylorConsts tc = taylor_consts(p);
         for (int f = 0; f < 2; ++f) {
             k_setupA<C><<<(KNt + 127) / 128, 128, 0, p->stream>>>(
-                reinterpret_cast<const double2*>(p->n2), KNt, p->Nz, p->ldz, tc.a[f], s, tc.einv[f],
-                reinterpret_cast<C*>(p->mz) + (size_t)f * KNt * p->ldz, p->status);
+                f == 0 ? src : reinterpret_cast<const double2*>(p->n2), f == 0 ? copy : nullptr, KNt, p->Nz,
+                p->ldz, tc.a[f], s, tc.einv[f], reinterpret_cast<C*>(p->mz) + (size_t)f * KNt * p->ldz, p->status);
             PE3D_CUDA(cudaGetLastError());
         }
         p->total_launches += 2;
         return PE3D_OK;
     }
-    k_setupA<C><<<(KNt + 127) / 128, 128, 0, p->stream>>>(
-        reinterpret_cast<const double2*>(p->n2), KNt, p->Nz, p->ldz, alpha, s, einv,
-        reinterpret_cast<C*>(p->mz), p->status);
+    k_setupA<C><<<(KNt + 127) / 128, 128, 0, p->stream>>>(src, copy, KNt, p->Nz, p->ldz, alpha, s, einv,
+                                                           reinterpret_cast<C*>(p->mz), p->status);
     PE3D_CUDA(cudaGetLastError());
     p->total_launches += 1;
     return PE3D_OK;

@@ -95,6 +95,9 @@ struct pe3d_server_s {
     int64_t n_submitted = 0, n_admitted = 0, n_finished = 0, n_failed = 0, n_ticks = 0, point_steps = 0;
     int64_t setup_launches = 0;           // kernels the admission thread launched (set-up of each request)
     int64_t tick_launches = 0;            // kernels of the batched turns (the owner plan's count)
+    int64_t tick_us = 0;                  // scheduler time in turns (launch, wait, retire)
+    int64_t kernel_us = 0;                // GPU time of the turns' launches (events on the server stream)
+    cudaEvent_t ev_a = nullptr, ev_b = nullptr;
 
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -214,8 +217,10 @@ bool pe3d_server_s::tick() {
         act = active;
     }
     if (act.empty()) return false;
+    const auto tw0 = std::chrono::steady_clock::now();
     bool ok = true;
     std::string why;
+    cudaEventRecord(ev_a, stream);
     for (int prec : {PE3D_FP32, PE3D_FP64}) {
         std::vector<Request*> grp;
         for (Request* q : act)
@@ -250,15 +255,22 @@ bool pe3d_server_s::tick() {
             if (ce != cudaSuccess) { ok = false; why = cudaGetErrorString(ce); }
         }
     }
+    cudaEventRecord(ev_b, stream);
     int st = 0;
     if (ok) {
         cudaError_t ce = cudaMemcpy(&st, owner->status, sizeof(int), cudaMemcpyDeviceToHost);
         if (ce != cudaSuccess || st != 0) { ok = false; why = "device status " + std::to_string(st); }
     }
+    float kms = 0.f;
+    if (cudaEventSynchronize(ev_b) != cudaSuccess || cudaEventElapsedTime(&kms, ev_a, ev_b) != cudaSuccess) {
+        cudaGetLastError();
+        kms = 0.f;
+    }
     {
         std::lock_guard<std::mutex> lk(mu);
         ++n_ticks;
         tick_launches = owner->total_launches;
+        kernel_us += (int64_t)(kms * 1e3f);
     }
     std::vector<Request*> done;
     for (Request* q : act) {
@@ -277,6 +289,11 @@ bool pe3d_server_s::tick() {
         cudaMemset(owner->status, 0, sizeof(int));
     }
     if (!done.empty()) cv.notify_all();   // memory freed: the admission thread may take the next request
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        tick_us += std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - tw0)
+                       .count();
+    }
     return true;
 }
 
@@ -352,9 +369,20 @@ int pe3d_server_create(size_t mem_budget, int max_active, int chunk, pe3d_server
     s->t0 = std::chrono::steady_clock::now();
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
-    if (e != cudaSuccess) return cuda_fail(e, "server stream");
+    if (e == cudaSuccess) e = cudaEventCreate(&s->ev_a);
+    if (e == cudaSuccess) e = cudaEventCreate(&s->ev_b);
+    if (e != cudaSuccess) {
+        if (s->ev_a) cudaEventDestroy(s->ev_a);
+        if (s->stream) cudaStreamDestroy(s->stream);
+        return cuda_fail(e, "server stream");
+    }
     int rc = pe3d_plan(1, 1, 1.0, 1.0, 1.0, 1.0, PE3D_WALLED, PE3D_FP32, s->stream, &s->owner);
-    if (rc) { cudaStreamDestroy(s->stream); return rc; }
+    if (rc) {
+        cudaEventDestroy(s->ev_a);
+        cudaEventDestroy(s->ev_b);
+        cudaStreamDestroy(s->stream);
+        return rc;
+    }
     pe3d_server_s* raw = s.release();
     raw->th = std::thread([raw] { raw->loop(); });
     raw->admit_th = std::thread([raw] { raw->admit_loop(); });
@@ -432,8 +460,8 @@ int pe3d_server_stats(pe3d_server_t s, int64_t* stats, int n) {
     if (!s || !stats || n < 0) return fail(PE3D_ERR_ARG, "bad argument");
     std::lock_guard<std::mutex> lk(s->mu);
     const int64_t v[] = {s->n_submitted, s->n_admitted, s->n_finished, s->n_failed, s->n_ticks, s->point_steps,
-                         (int64_t)s->used, s->setup_launches + s->tick_launches};
-    const int cnt = std::min<int>(n, 8);
+                         (int64_t)s->used, s->setup_launches + s->tick_launches, s->tick_us, s->kernel_us};
+    const int cnt = std::min<int>(n, 10);
     for (int i = 0; i < cnt; ++i) stats[i] = v[i];
     return cnt;
 }
@@ -459,6 +487,8 @@ int pe3d_server_destroy(pe3d_server_t s) {
         if (q->stream) cudaStreamDestroy(q->stream);
     }
     if (s->owner) pe3d_destroy(s->owner);
+    if (s->ev_a) cudaEventDestroy(s->ev_a);
+    if (s->ev_b) cudaEventDestroy(s->ev_b);
     if (s->stream) cudaStreamDestroy(s->stream);
     delete s;
     return PE3D_OK;

@@ -98,8 +98,9 @@ int run_static(pe3d_plan_s& p, const pe3d_host::StaticKernels& kt, unsigned char
     double2 einv = make_double2(ev.x / en, -ev.y / en);
     const double2* n2d = reinterpret_cast<const double2*>(n2);
     int KNt = sr.K * p.Nt, Nz = p.Nz, ldz = p.ldz;
+    double2* no_copy = nullptr;
     {
-        void* args[] = {&n2d, &KNt, &Nz, &ldz, (void*)&alpha, (void*)&s, &einv, &mz, &status};
+        void* args[] = {&n2d, &no_copy, &KNt, &Nz, &ldz, (void*)&alpha, (void*)&s, &einv, &mz, &status};
         if ((e = cudaLaunchKernel(kt.setupA, dim3((KNt + 127) / 128), dim3(128), args, 0, st)) != cudaSuccess)
             return cuda_fail(e, "setup of the depth systems");
     }
