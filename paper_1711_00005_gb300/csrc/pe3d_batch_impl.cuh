@@ -27,6 +27,30 @@ struct BatchTable {
     }
 };
 
+// Prefer the smallest shared-memory carveout that still holds nb CTAs of
+// `smem` dynamic bytes (with the kernel's static shared memory and the
+// per-block reservation), so the rest of the SM's unified L1 caches what the
+// batched kernels read through it on every unit: the marches' descriptors and
+// per-step tables.  At the maximal carveout (100) L1 keeps about 28 KB, less
+// than 40 descriptors.  Restores 100 if the occupancy calculator then finds
+// fewer than nb CTAs per SM.
+inline cudaError_t l1_carveout(const void* fn, int nb, size_t smem) {
+    int dev = 0, per_sm = 0, reserved = 0;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess || per_sm <= 0) return e;
+    const size_t want = (size_t)nb * (smem + fa.sharedSizeBytes + (size_t)reserved);
+    const int pct = (int)std::min<size_t>(100, (want * 100 + (size_t)per_sm - 1) / (size_t)per_sm);
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, pct)) != cudaSuccess) return e;
+    int nb2 = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, fn, NT, smem)) != cudaSuccess) return e;
+    if (nb2 < nb) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    return e;
+}
+
 // the batched kernels, with their shared-memory limits set once per device context
 template <typename C>
 int batch_kernels(const BatchTable<C>** out) {
@@ -105,8 +129,10 @@ int launch_batched(pe3d_plan_s* owner, std::vector<MarchArgs<C>>& descs, int nst
     if (rc0) return rc0;
     const void* fn = bt->k[ca][cb];
     int nb = 0;
+    PE3D_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     PE3D_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, NT, smem));
     if (nb < 1) return fail(PE3D_ERR_ARG, "batched kernel does not fit on an SM");
+    PE3D_CUDA(l1_carveout(fn, nb, smem));
     const int grid = std::min(nb * owner->num_sms, std::max(pref[n], pref[2 * n + 1]));
     const MarchArgs<C>* dd = reinterpret_cast<const MarchArgs<C>*>(b);
     const int* dp = reinterpret_cast<const int*>(b + dbytes);
