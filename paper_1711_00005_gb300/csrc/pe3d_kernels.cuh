@@ -184,10 +184,12 @@ __host__ inline bool plan_smem(int NG, int ldz, int rowsB, int TZ, int NtP, int 
 // ---------------------------------------------------------------------------
 
 // thread 0: copy the unit's columns of w (and of the slice's multipliers if
-// with_mu) into phase-A buffer `buf`
+// with_mu) into phase-A buffer `buf`.  fence = false when thread 0 has already
+// run the shared-memory proxy fence after the CTA's last generic access of
+// the buffer (the persistent march does it while it waits at a grid barrier).
 template <typename C>
 __device__ __forceinline__ void loadA(const MarchArgs<C>& P, int slice, int base, unsigned char* smem, int buf,
-                                      bool with_mu, uint32_t& par) {
+                                      bool with_mu, uint32_t& par, bool fence = true) {
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem) + MB_A + buf;
     par |= 1u << (INFLIGHT + MB_A + buf);
     const int ldz = P.ldz;
@@ -195,7 +197,7 @@ __device__ __forceinline__ void loadA(const MarchArgs<C>& P, int slice, int base
     const C* mz = P.mz + (long long)slice * P.slice_stride;
     const int nact = min(P.NG, P.Nt - base);
     const uint32_t colb = (uint32_t)(ldz * sizeof(C));
-    fence_proxy_async_smem();
+    if (fence) fence_proxy_async_smem();
     mbar_arrive_expect_tx(mbar, (with_mu ? 2u : 1u) * nact * colb);
     for (int g = 0; g < nact; ++g) {
         C* dw = reinterpret_cast<C*>(smem + P.sp.a[buf] + g * gstride);
@@ -476,15 +478,16 @@ __device__ __forceinline__ void prefetch_coefB(const MarchArgs<C>& P, int j, uns
 }
 // thread 0: the tile of v (TMA boxes of BY rows; rows past Nt arrive as
 // zeros) into B buffer `buf`, with the step's coefficient rows into region
-// buf if with_coef
+// buf if with_coef; fence as in loadA
 template <typename C>
 __device__ __forceinline__ void loadB(const MarchArgs<C>& P, const CUtensorMap* tmap, int j, int tile,
-                                      unsigned char* smem, int buf, bool with_coef, uint32_t& par) {
+                                      unsigned char* smem, int buf, bool with_coef, uint32_t& par,
+                                      bool fence = true) {
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem) + MB_B + buf;
     par = (par | (1u << (INFLIGHT + MB_B + buf))) & ~(1u << (PENDING + MB_B + buf));
     C* tl = reinterpret_cast<C*>(smem + P.sp.b[buf]);
     const uint32_t boxb = (uint32_t)(P.BY * P.TZ * sizeof(C));
-    fence_proxy_async_smem();
+    if (fence) fence_proxy_async_smem();
     mbar_arrive_expect_tx(mbar, P.nload * boxb + (with_coef ? coefB_bytes(P) : 0u));
     const int x = tile * P.TZ * (int)(sizeof(C) / 8);
     for (int q = 0; q < P.nload; ++q) tma_g2s_2d(tl + (size_t)q * P.BY * P.TZ, tmap, x, q * P.BY, mbar);
@@ -971,6 +974,7 @@ __global__ void __launch_bounds__(NT) k_march_persistent(const __grid_constant__
     // thread 0 reads the next step's slice one step ahead
     int sl_next = (threadIdx.x == 0 && P.j0 < P.j1) ? P.slice_of_step[P.j0] : 0;
     int sl_held = -1;                                 // slice of the multipliers in a[0] (keepA)
+    bool fenced = false;                              // thread 0 ran the proxy fence during the last barrier
     if (threadIdx.x == 0 && hasB && P.j0 < P.j1) prefetch_coefB(P, P.j0, smem, 0, 0, par);
     auto nextA = [&](int u) { return u + G < unitsA ? u + G : -1; };
     auto nextB = [&](int t) { return t + G < P.tiles ? t + G : -1; };
@@ -989,7 +993,7 @@ __global__ void __launch_bounds__(NT) k_march_persistent(const __grid_constant__
             }
         } else {
             if (hasA && threadIdx.x == 0) {
-                loadA(P, sl, bid * P.NG, smem, 0, !(keepA && sl == sl_held), par);
+                loadA(P, sl, bid * P.NG, smem, 0, !(keepA && sl == sl_held), par, !fenced);
                 sl_held = keepA ? sl : -1;
             }
             // read after the copies are issued: their proxy fence would wait for it
@@ -1003,11 +1007,14 @@ __global__ void __launch_bounds__(NT) k_march_persistent(const __grid_constant__
             }
         }
         PE3D_MARK(16);
-        if (!grid_barrier(P.bar, (++nb) * G, P.status, P.spin_limit)) PE3D_ABORT();
+        grid_arrive(P.bar);
+        // the proxy fence of the first tile's copy, while the barrier completes
+        if (threadIdx.x == 0 && hasB) fence_proxy_async_smem();
+        if (!grid_wait(P.bar, (++nb) * G, P.status, P.spin_limit)) PE3D_ABORT();
         PE3D_MARK(17);
         // phase B (Eq. 6)
         if (hasB) {
-            if (threadIdx.x == 0) loadB(P, &P.tmap_v, j, bid, smem, 0, false, par);
+            if (threadIdx.x == 0) loadB(P, &P.tmap_v, j, bid, smem, 0, false, par, false);
             const bool ok = unit_pipeline(
                 bid, P.sp.nbufB,
                 [&](int t, int b) { loadB(P, &P.tmap_v, j, t, smem, b, false, par); },
@@ -1017,8 +1024,14 @@ __global__ void __launch_bounds__(NT) k_march_persistent(const __grid_constant__
         PE3D_MARK(18);
         const bool refine = P.rc_every > 0 && (j + 1) % P.rc_every == 0;
         grid_arrive(P.bar);
-        // the next step's azimuth coefficients, while the barrier completes
-        if (threadIdx.x == 0 && hasB && !refine && j + 1 < P.j1) prefetch_coefB(P, j + 1, smem, 0, 0, par);
+        // the next step's azimuth coefficients, while the barrier completes;
+        // their copy's proxy fence also serves the next depth unit's copy
+        fenced = false;
+        if (threadIdx.x == 0 && !refine && j + 1 < P.j1) {
+            if (hasB) prefetch_coefB(P, j + 1, smem, 0, 0, par);
+            else if (hasA) fence_proxy_async_smem();
+            fenced = true;
+        }
         if (!grid_wait(P.bar, (++nb) * G, P.status, P.spin_limit)) PE3D_ABORT();
         PE3D_MARK(19);
         if constexpr (!TAYLOR) {
@@ -1162,55 +1175,70 @@ __global__ void __launch_bounds__(NT, 2) k_march_batched(const MarchArgs<C>* __r
     const int nbufA = D[0].sp.nbufA, nbufB = D[0].sp.nbufB;   // one shared-memory plan for the batch
     const long long lim = D[0].spin_limit;                     // the first plan's wait limit
     unsigned nb = 0;
+    // A CTA takes units blockIdx.x, + G, ... of each phase, so the march of its
+    // units only moves forward: cursors (one for the copies thread 0 issues a
+    // unit ahead, one for the unit being solved, one for the search for the
+    // next active unit) replace a binary search per unit.
+    auto advance = [&](const int* pf, int& i, int u) {
+        while (i + 1 < n && pf[i + 1] <= u) ++i;
+        return i;
+    };
     for (int t = t_begin; t < t_end; ++t) {
+        int ia_next = 0, ia_load = 0, ia_comp = 0, ib_next = 0, ib_load = 0, ib_comp = 0;
         // the next unit, from u on in steps of G, of a march inside its window
         auto activeA = [&](int u) {
             for (; u < s_pa[n]; u += G) {
-                const int i = find_march(s_pa, n, u);
+                const int i = advance(s_pa, ia_next, u);
                 if (s_j0[i] + t < s_j1[i]) return u;
             }
             return -1;
         };
         auto activeB = [&](int u) {
             for (; u < s_pb[n]; u += G) {
-                const int i = find_march(s_pb, n, u);
+                const int i = advance(s_pb, ib_next, u);
                 if (s_j0[i] + t < s_j1[i]) return u;
             }
             return -1;
         };
-        auto loadUA = [&](int u, int b) {
-            const int i = find_march(s_pa, n, u);
-            loadA(D[i], D[i].slice_of_step[s_j0[i] + t], (u - s_pa[i]) * D[i].NG, smem, b, true, par);
+        // fence = false for a phase's first unit: thread 0 ran the proxy fence
+        // while it waited at the grid barrier before the phase
+        auto loadUA = [&](int u, int b, bool fence) {
+            const int i = advance(s_pa, ia_load, u);
+            loadA(D[i], D[i].slice_of_step[s_j0[i] + t], (u - s_pa[i]) * D[i].NG, smem, b, true, par, fence);
         };
-        auto loadUB = [&](int u, int b) {
-            const int i = find_march(s_pb, n, u);
-            loadB(D[i], &D[i].tmap_v, s_j0[i] + t, u - s_pb[i], smem, b, true, par);
+        auto loadUB = [&](int u, int b, bool fence) {
+            const int i = advance(s_pb, ib_load, u);
+            loadB(D[i], &D[i].tmap_v, s_j0[i] + t, u - s_pb[i], smem, b, true, par, fence);
         };
         const int fa = activeA(blockIdx.x);
-        if (fa >= 0 && threadIdx.x == 0) loadUA(fa, 0);
+        if (fa >= 0 && threadIdx.x == 0) loadUA(fa, 0, t == t_begin);
         bool ok = unit_pipeline(
-            fa, nbufA, loadUA,
+            fa, nbufA, [&](int u, int b) { loadUA(u, b, true); },
             [&](int u, int b) {
-                const int i = find_march(s_pa, n, u);
+                const int i = advance(s_pa, ia_comp, u);
                 return computeA<C, LA>(D[i], (u - s_pa[i]) * D[i].NG, smem, b, par);
             },
             [&](int u) { return activeA(u + G); });
         if (!ok) PE3D_ABORT();
         PE3D_MARK(16);
-        if (!grid_barrier(bar, (++nb) * G, status, lim)) PE3D_ABORT();
+        grid_arrive(bar);
+        if (threadIdx.x == 0) fence_proxy_async_smem();   // for the first tile's copy
+        if (!grid_wait(bar, (++nb) * G, status, lim)) PE3D_ABORT();
         PE3D_MARK(17);
         const int fb = activeB(blockIdx.x);
-        if (fb >= 0 && threadIdx.x == 0) loadUB(fb, 0);
+        if (fb >= 0 && threadIdx.x == 0) loadUB(fb, 0, false);
         ok = unit_pipeline(
-            fb, nbufB, loadUB,
+            fb, nbufB, [&](int u, int b) { loadUB(u, b, true); },
             [&](int u, int b) {
-                const int i = find_march(s_pb, n, u);
+                const int i = advance(s_pb, ib_comp, u);
                 return computeB<C, LB>(D[i], s_j0[i] + t, u - s_pb[i], smem, b, b, par);
             },
             [&](int u) { return activeB(u + G); });
         if (!ok) PE3D_ABORT();
         PE3D_MARK(18);
-        if (!grid_barrier(bar, (++nb) * G, status, lim)) PE3D_ABORT();
+        grid_arrive(bar);
+        if (threadIdx.x == 0) fence_proxy_async_smem();   // for the next step's first depth unit
+        if (!grid_wait(bar, (++nb) * G, status, lim)) PE3D_ABORT();
         PE3D_MARK(19);
     }
 }
