@@ -63,22 +63,27 @@ int layout_choose(pe3d_plan_s* p) {
     p->ldz = p->T * p->L;
     p->NG = NT / p->T;
 
+    // The first tile width whose azimuth chunks fit in 17 rows, else in 33:
+    // the kernels built for 33-row chunks spill at two CTAs per SM, and one
+    // such march sets the variant of a whole batch.
     const int tz_cand[5] = {8, 16, 32, 4, 2};
     int tz = -1;
-    for (int ci = 0; ci < 5; ++ci) {
-        const int TZ = tz_cand[ci];
-        if (p->ttile && TZ != p->ttile) continue;
-        const int K = NT / TZ;
-        const int Lt = odd_ceil(p->Nt, K);
-        const int nload = (p->Nt + 255) / 256;
-        const int BY = box_rows(p->Nt, nload, (int)(TZ * sizeof(C)));
-        const int rowsB = std::max(K * Lt, nload * BY);
-        SmemPlan sp;
-        if (Lt > 33 || !plan_smem<C>(p->NG, p->ldz, rowsB, TZ, K * Lt, p->boundary == PE3D_PERIODIC, false, false,
-                                     false, false, SMEM_BUDGET, &sp))
-            continue;
-        tz = TZ;
-        break;
+    for (int lmax : {17, 33}) {
+        for (int ci = 0; ci < 5 && tz < 0; ++ci) {
+            const int TZ = tz_cand[ci];
+            if (p->ttile && TZ != p->ttile) continue;
+            const int K = NT / TZ;
+            const int Lt = odd_ceil(p->Nt, K);
+            const int nload = (p->Nt + 255) / 256;
+            const int BY = box_rows(p->Nt, nload, (int)(TZ * sizeof(C)));
+            const int rowsB = std::max(K * Lt, nload * BY);
+            SmemPlan sp;
+            if (Lt > lmax || !plan_smem<C>(p->NG, p->ldz, rowsB, TZ, K * Lt, p->boundary == PE3D_PERIODIC, false,
+                                           false, false, false, SMEM_BUDGET, &sp))
+                continue;
+            tz = TZ;
+        }
+        if (tz >= 0) break;
     }
     if (tz < 0) return fail(PE3D_ERR_ARG, "azimuth systems too long (at most 33 points per thread) or the tile "
                                           "too large for the shared-memory budget");
