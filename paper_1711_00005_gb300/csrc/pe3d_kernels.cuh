@@ -52,6 +52,8 @@ constexpr int ST_TIMEOUT = -4;    // PE3D_ERR_TIMEOUT
 // its arrival) so that an aborting CTA can drain them.
 constexpr int MB_A = 0, MB_B = 2;
 constexpr uint32_t INFLIGHT = 8, PENDING = 12;
+// thread 0 has bulk stores of v outstanding (computeA's bulk_store)
+constexpr uint32_t BULK = 1u << 16;
 
 // Byte offsets of the shared-memory regions of one CTA.  Phase-B tiles may
 // overlap the phase-A buffers (the grid barrier separates the phases); the
@@ -187,7 +189,9 @@ __host__ inline bool plan_smem(int NG, int ldz, int rowsB, int TZ, int NtP, int 
 // with_mu) into phase-A buffer `buf`.  fence = false when thread 0 has already
 // run the shared-memory proxy fence after the CTA's last generic access of
 // the buffer (the persistent march does it while it waits at a grid barrier).
-template <typename C>
+// AFTER_BULK: the kernel stores v with bulk copies (computeA's BULK_STORE),
+// whose sources must be read before the buffer is refilled.
+template <typename C, bool AFTER_BULK = false>
 __device__ __forceinline__ void loadA(const MarchArgs<C>& P, int slice, int base, unsigned char* smem, int buf,
                                       bool with_mu, uint32_t& par, bool fence = true) {
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem) + MB_A + buf;
@@ -197,6 +201,8 @@ __device__ __forceinline__ void loadA(const MarchArgs<C>& P, int slice, int base
     const C* mz = P.mz + (long long)slice * P.slice_stride;
     const int nact = min(P.NG, P.Nt - base);
     const uint32_t colb = (uint32_t)(ldz * sizeof(C));
+    if constexpr (AFTER_BULK)   // the bulk stores of v out of this buffer have read it
+        if (par & BULK) bulk_wait_read();
     if (fence) fence_proxy_async_smem();
     mbar_arrive_expect_tx(mbar, (with_mu ? 2u : 1u) * nact * colb);
     for (int g = 0; g < nact; ++g) {
@@ -209,7 +215,7 @@ __device__ __forceinline__ void loadA(const MarchArgs<C>& P, int slice, int base
 // Solve the unit in buffer `buf` (v over w in place) and store its columns of
 // v.  Returns false (uniformly across the CTA) if the bounded wait for the
 // buffer gave up; on return the buffer is free for the next copy.
-template <typename C, int LA>
+template <typename C, int LA, bool BULK_STORE = false>
 __device__ bool computeA(const MarchArgs<C>& P, int base, unsigned char* smem, int buf, uint32_t& par) {
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem) + MB_A + buf;
     const int tid = threadIdx.x;
@@ -309,11 +315,29 @@ __device__ bool computeA(const MarchArgs<C>& P, int base, unsigned char* smem, i
     } else {
         passes(std::false_type{});
     }
+    if constexpr (BULK_STORE) fence_proxy_async_smem();   // v, written over w, is read by the bulk stores below
     __syncthreads();
     PE3D_MARK(6);
 
-    // 3. store the unit's columns of v (16-B coalesced), then free the buffer
-    {
+    // 3. store the unit's columns of v.  BULK_STORE (another unit of this CTA
+    // follows in the phase): thread 0 issues one bulk copy per column (ldz is
+    // even, so every column is a multiple of 16 B) and the CTA moves on; the
+    // buffer is free once their sources are read, which the next copy into it
+    // waits for (loadA, loadB), and thread 0 waits for their completion
+    // before it arrives at the grid barrier (bulk_settle).  Otherwise (the
+    // phase's last unit, whose
+    // stores the barrier waits for anyway) all threads store with 16-B
+    // coalesced stores, which finishes sooner than one copy engine.
+    if constexpr (BULK_STORE) {
+        if (tid == 0) {
+            const int nact = min(P.NG, P.Nt - base);
+            const uint32_t colb = (uint32_t)(ldz * sizeof(C));
+            for (int gg = 0; gg < nact; ++gg)
+                bulk_s2g(P.v + (size_t)(base + gg) * ldz, smem + P.sp.a[buf] + gg * gstride, colb);
+            bulk_commit();
+            par |= BULK;
+        }
+    } else {
         const int nact = min(P.NG, P.Nt - base);
         const int n16 = (int)(ldz * sizeof(C) / 16);
         const float4* s4 = reinterpret_cast<const float4*>(smem + P.sp.a[buf]);
@@ -322,8 +346,8 @@ __device__ bool computeA(const MarchArgs<C>& P, int base, unsigned char* smem, i
             const int gg = i / n16, e = i - gg * n16;
             __stcg(reinterpret_cast<float4*>(P.v + (size_t)(base + gg) * ldz) + e, s4[gg * g16 + e]);
         }
+        __syncthreads();
     }
-    __syncthreads();
     PE3D_MARK(7);
     return true;
 }
@@ -479,7 +503,7 @@ __device__ __forceinline__ void prefetch_coefB(const MarchArgs<C>& P, int j, uns
 // thread 0: the tile of v (TMA boxes of BY rows; rows past Nt arrive as
 // zeros) into B buffer `buf`, with the step's coefficient rows into region
 // buf if with_coef; fence as in loadA
-template <typename C>
+template <typename C, bool AFTER_BULK = false>
 __device__ __forceinline__ void loadB(const MarchArgs<C>& P, const CUtensorMap* tmap, int j, int tile,
                                       unsigned char* smem, int buf, bool with_coef, uint32_t& par,
                                       bool fence = true) {
@@ -487,6 +511,8 @@ __device__ __forceinline__ void loadB(const MarchArgs<C>& P, const CUtensorMap* 
     par = (par | (1u << (INFLIGHT + MB_B + buf))) & ~(1u << (PENDING + MB_B + buf));
     C* tl = reinterpret_cast<C*>(smem + P.sp.b[buf]);
     const uint32_t boxb = (uint32_t)(P.BY * P.TZ * sizeof(C));
+    if constexpr (AFTER_BULK)   // tiles may share memory with the depth buffers
+        if (par & BULK) bulk_wait_read();
     if (fence) fence_proxy_async_smem();
     mbar_arrive_expect_tx(mbar, P.nload * boxb + (with_coef ? coefB_bytes(P) : 0u));
     const int x = tile * P.TZ * (int)(sizeof(C) / 8);
@@ -680,6 +706,7 @@ __device__ bool computeB(const MarchArgs<C>& P, int j, int tile, unsigned char* 
 // before its arrival is arrived on first).
 __device__ __forceinline__ void drain_copies(unsigned char* smem, uint32_t par) {
     if (threadIdx.x != 0) return;
+    if (par & BULK) bulk_wait();   // bulk stores out of shared memory complete before the CTA leaves
     uint64_t* mb = reinterpret_cast<uint64_t*>(smem);
     for (int i = 0; i < 4; ++i) {
         if (par & (1u << (PENDING + i)))
@@ -755,6 +782,15 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
 // polls (SPIN_LIMIT unless the plan sets PE3D_OPT_WAIT_LIMIT), or once
 // another CTA has flagged an error, it records PE3D_ERR_TIMEOUT and returns
 // false.
+// thread 0, before a grid barrier that follows depth units: its bulk stores
+// of v complete before its release (the wait is skipped when none were
+// issued: even with nothing outstanding it costs tens of cycles)
+__device__ __forceinline__ void bulk_settle(uint32_t& par) {
+    if (threadIdx.x == 0 && (par & BULK)) {
+        bulk_wait();
+        par &= ~BULK;
+    }
+}
 __device__ __forceinline__ void grid_arrive(unsigned* ctr) {
     asm volatile("fence.proxy.async.global;" ::: "memory");
     __syncthreads();
@@ -938,10 +974,11 @@ __device__ void combine_phase(const MarchArgs<C>& P, int j) {
 // grid barriers per step (six on a corrected step)
 // ---------------------------------------------------------------------------
 
-// Run `compute(u, buf)` on units first, next(first), ... (next returns -1 at
-// the end), with thread 0 issuing `load(u, buf)` one unit ahead when there
-// are two buffers, or right after the previous unit with one (compute
-// returns with its buffer free).  The caller has issued load(first, 0).
+// Run `compute(u, buf, more)` on units first, next(first), ... (next returns
+// -1 at the end; more says whether another unit follows), with thread 0
+// issuing `load(u, buf)` one unit ahead when there are two buffers, or right
+// after the previous unit with one (compute returns with its buffer free, or
+// with its bulk stores issued).  The caller has issued load(first, 0).
 template <typename Load, typename Compute, typename Next>
 __device__ __forceinline__ bool unit_pipeline(int first, int nbuf, Load load, Compute compute, Next next) {
     int u = first, n = 0;
@@ -949,7 +986,7 @@ __device__ __forceinline__ bool unit_pipeline(int first, int nbuf, Load load, Co
         const int un = next(u);
         const int buf = nbuf > 1 ? (n & 1) : 0;
         if (nbuf > 1 && un >= 0 && threadIdx.x == 0) load(un, buf ^ 1);
-        if (!compute(u, buf)) return false;
+        if (!compute(u, buf, un >= 0)) return false;
         if (nbuf == 1 && un >= 0 && threadIdx.x == 0) load(un, 0);
         u = un;
         ++n;
@@ -999,10 +1036,13 @@ __global__ void __launch_bounds__(NT) k_march_persistent(const __grid_constant__
             // read after the copies are issued: their proxy fence would wait for it
             if (threadIdx.x == 0 && j + 1 < P.j1) sl_next = P.slice_of_step[j + 1];
             if (hasA) {
+                // coalesced stores of v by all threads (no bulk stores: measured
+                // on the 100 Hz and 200 Hz grids, they gained 0.8 % where a CTA
+                // has several depth units and cost 0.7 % where it has one)
                 const bool ok = unit_pipeline(
                     bid, P.sp.nbufA,
                     [&](int u, int b) { loadA(P, sl, u * P.NG, smem, b, true, par); },
-                    [&](int u, int b) { return computeA<C, LA>(P, u * P.NG, smem, b, par); }, nextA);
+                    [&](int u, int b, bool) { return computeA<C, LA>(P, u * P.NG, smem, b, par); }, nextA);
                 if (!ok) PE3D_ABORT();
             }
         }
@@ -1018,7 +1058,7 @@ __global__ void __launch_bounds__(NT) k_march_persistent(const __grid_constant__
             const bool ok = unit_pipeline(
                 bid, P.sp.nbufB,
                 [&](int t, int b) { loadB(P, &P.tmap_v, j, t, smem, b, false, par); },
-                [&](int t, int b) { return computeB<C, LB>(P, j, t, smem, b, 0, par); }, nextB);
+                [&](int t, int b, bool) { return computeB<C, LB>(P, j, t, smem, b, 0, par); }, nextB);
             if (!ok) PE3D_ABORT();
         }
         PE3D_MARK(18);
@@ -1204,23 +1244,25 @@ __global__ void __launch_bounds__(NT, 2) k_march_batched(const MarchArgs<C>* __r
         // while it waited at the grid barrier before the phase
         auto loadUA = [&](int u, int b, bool fence) {
             const int i = advance(s_pa, ia_load, u);
-            loadA(D[i], D[i].slice_of_step[s_j0[i] + t], (u - s_pa[i]) * D[i].NG, smem, b, true, par, fence);
+            loadA<C, true>(D[i], D[i].slice_of_step[s_j0[i] + t], (u - s_pa[i]) * D[i].NG, smem, b, true, par, fence);
         };
         auto loadUB = [&](int u, int b, bool fence) {
             const int i = advance(s_pb, ib_load, u);
-            loadB(D[i], &D[i].tmap_v, s_j0[i] + t, u - s_pb[i], smem, b, true, par, fence);
+            loadB<C, true>(D[i], &D[i].tmap_v, s_j0[i] + t, u - s_pb[i], smem, b, true, par, fence);
         };
         const int fa = activeA(blockIdx.x);
         if (fa >= 0 && threadIdx.x == 0) loadUA(fa, 0, t == t_begin);
         bool ok = unit_pipeline(
             fa, nbufA, [&](int u, int b) { loadUA(u, b, true); },
-            [&](int u, int b) {
+            [&](int u, int b, bool more) {
                 const int i = advance(s_pa, ia_comp, u);
-                return computeA<C, LA>(D[i], (u - s_pa[i]) * D[i].NG, smem, b, par);
+                return more ? computeA<C, LA, true>(D[i], (u - s_pa[i]) * D[i].NG, smem, b, par)
+                            : computeA<C, LA>(D[i], (u - s_pa[i]) * D[i].NG, smem, b, par);
             },
             [&](int u) { return activeA(u + G); });
         if (!ok) PE3D_ABORT();
         PE3D_MARK(16);
+        bulk_settle(par);
         grid_arrive(bar);
         if (threadIdx.x == 0) fence_proxy_async_smem();   // for the first tile's copy
         if (!grid_wait(bar, (++nb) * G, status, lim)) PE3D_ABORT();
@@ -1229,7 +1271,7 @@ __global__ void __launch_bounds__(NT, 2) k_march_batched(const MarchArgs<C>* __r
         if (fb >= 0 && threadIdx.x == 0) loadUB(fb, 0, false);
         ok = unit_pipeline(
             fb, nbufB, [&](int u, int b) { loadUB(u, b, true); },
-            [&](int u, int b) {
+            [&](int u, int b, bool) {
                 const int i = advance(s_pb, ib_comp, u);
                 return computeB<C, LB>(D[i], s_j0[i] + t, u - s_pb[i], smem, b, b, par);
             },
