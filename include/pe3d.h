@@ -256,7 +256,9 @@ int pe3d_march_batched(int n, const pe3d_plan_t *plans, const void *const *u0, c
  *   Every call reuses the same array and leaves its contents behind; each call
  *   clears what must start at zero.  Calls that overlap on the GPU (two host
  *   threads, or two streams) race on the array: serialise them.  The call
- *   returns after its stream has finished the march.
+ *   synchronises its stream (it reads the status word back) and returns after
+ *   the march has finished, so it cannot be recorded in a CUDA graph: calling
+ *   it on a stream under capture fails with PE3D_ERR_CUDA.
  * Errors: PE3D_ERR_ARG, PE3D_ERR_SINGULAR, PE3D_ERR_TIMEOUT, PE3D_ERR_CUDA. */
 #define PE3D_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
 #define PE3D_STATIC_MAX_SLICES 256
