@@ -189,7 +189,7 @@ __host__ inline bool plan_smem(int NG, int ldz, int rowsB, int TZ, int NtP, int 
 // with_mu) into phase-A buffer `buf`.  fence = false when thread 0 has already
 // run the shared-memory proxy fence after the CTA's last generic access of
 // the buffer (the persistent march does it while it waits at a grid barrier).
-// AFTER_BULK: the kernel stores v with bulk copies (computeA's BULK_STORE),
+// AFTER_BULK: the kernel stores v with bulk copies (computeA's bulk_store),
 // whose sources must be read before the buffer is refilled.
 template <typename C, bool AFTER_BULK = false>
 __device__ __forceinline__ void loadA(const MarchArgs<C>& P, int slice, int base, unsigned char* smem, int buf,
@@ -215,8 +215,9 @@ __device__ __forceinline__ void loadA(const MarchArgs<C>& P, int slice, int base
 // Solve the unit in buffer `buf` (v over w in place) and store its columns of
 // v.  Returns false (uniformly across the CTA) if the bounded wait for the
 // buffer gave up; on return the buffer is free for the next copy.
-template <typename C, int LA, bool BULK_STORE = false>
-__device__ bool computeA(const MarchArgs<C>& P, int base, unsigned char* smem, int buf, uint32_t& par) {
+template <typename C, int LA, bool CAN_BULK = false>
+__device__ bool computeA(const MarchArgs<C>& P, int base, unsigned char* smem, int buf, uint32_t& par,
+                         bool bulk_store = false) {
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem) + MB_A + buf;
     const int tid = threadIdx.x;
     const int gs = tid / P.T, k = tid - gs * P.T;
@@ -315,12 +316,14 @@ __device__ bool computeA(const MarchArgs<C>& P, int base, unsigned char* smem, i
     } else {
         passes(std::false_type{});
     }
-    if constexpr (BULK_STORE) fence_proxy_async_smem();   // v, written over w, is read by the bulk stores below
+    if constexpr (CAN_BULK)
+        if (bulk_store) fence_proxy_async_smem();   // v, written over w, is read by the bulk stores below
     __syncthreads();
     PE3D_MARK(6);
 
-    // 3. store the unit's columns of v.  BULK_STORE (another unit of this CTA
-    // follows in the phase): thread 0 issues one bulk copy per column (ldz is
+    // 3. store the unit's columns of v.  bulk_store (another unit of this CTA
+    // follows in the phase; only in kernels built with CAN_BULK, one instance
+    // for both paths): thread 0 issues one bulk copy per column (ldz is
     // even, so every column is a multiple of 16 B) and the CTA moves on; the
     // buffer is free once their sources are read, which the next copy into it
     // waits for (loadA, loadB), and thread 0 waits for their completion
@@ -328,7 +331,9 @@ __device__ bool computeA(const MarchArgs<C>& P, int base, unsigned char* smem, i
     // phase's last unit, whose
     // stores the barrier waits for anyway) all threads store with 16-B
     // coalesced stores, which finishes sooner than one copy engine.
-    if constexpr (BULK_STORE) {
+    bool bulk = false;
+    if constexpr (CAN_BULK) bulk = bulk_store;
+    if (bulk) {
         if (tid == 0) {
             const int nact = min(P.NG, P.Nt - base);
             const uint32_t colb = (uint32_t)(ldz * sizeof(C));
@@ -1256,8 +1261,7 @@ __global__ void __launch_bounds__(NT, 2) k_march_batched(const MarchArgs<C>* __r
             fa, nbufA, [&](int u, int b) { loadUA(u, b, true); },
             [&](int u, int b, bool more) {
                 const int i = advance(s_pa, ia_comp, u);
-                return more ? computeA<C, LA, true>(D[i], (u - s_pa[i]) * D[i].NG, smem, b, par)
-                            : computeA<C, LA>(D[i], (u - s_pa[i]) * D[i].NG, smem, b, par);
+                return computeA<C, LA, true>(D[i], (u - s_pa[i]) * D[i].NG, smem, b, par, more);
             },
             [&](int u) { return activeA(u + G); });
         if (!ok) PE3D_ABORT();
