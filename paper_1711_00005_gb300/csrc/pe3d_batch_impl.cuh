@@ -8,19 +8,23 @@
 namespace pe3d_host {
 using namespace pe3d;
 
-// compiled (depth chunk, azimuth chunk) classes of the batched kernel: chunks
-// shorter than the class maximum are predicated
+// compiled (depth chunk, azimuth chunk) classes of the batched kernel, all
+// four (5, 9, 17, 33) in each direction: chunks shorter than the class
+// maximum are predicated, and a padded slot costs a full element of work
+// (small grids, such as the broadband runs' 7-row depth and 5-row azimuth
+// chunks, would otherwise run 9-element loops)
 template <typename C>
 struct BatchTable {
-    const void* k[3][3];
+    const void* k[4][4];
     // the FP64 residual correction of a batched step (FP32 marches only): one
     // instantiation at the largest chunks, shorter chunks predicated
     const void* refine;
     BatchTable() {
-#define PE3D_B(a, b) k[a][b] = (const void*)k_march_batched<C, CHUNK_MAX[a + 1], CHUNK_MAX[b + 1]>
-        PE3D_B(0, 0); PE3D_B(0, 1); PE3D_B(0, 2);
-        PE3D_B(1, 0); PE3D_B(1, 1); PE3D_B(1, 2);
-        PE3D_B(2, 0); PE3D_B(2, 1); PE3D_B(2, 2);
+#define PE3D_B(a, b) k[a][b] = (const void*)k_march_batched<C, CHUNK_MAX[a], CHUNK_MAX[b]>
+        PE3D_B(0, 0); PE3D_B(0, 1); PE3D_B(0, 2); PE3D_B(0, 3);
+        PE3D_B(1, 0); PE3D_B(1, 1); PE3D_B(1, 2); PE3D_B(1, 3);
+        PE3D_B(2, 0); PE3D_B(2, 1); PE3D_B(2, 2); PE3D_B(2, 3);
+        PE3D_B(3, 0); PE3D_B(3, 1); PE3D_B(3, 2); PE3D_B(3, 3);
 #undef PE3D_B
         if constexpr (sizeof(C) == 8) refine = (const void*)k_refine_batched<C, CHUNK_MAX[3], CHUNK_MAX[3]>;
         else refine = nullptr;
@@ -56,8 +60,8 @@ template <typename C>
 int batch_kernels(const BatchTable<C>** out) {
     static const BatchTable<C> t;
     if (!context_prepared(&t)) {
-        for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) {
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b) {
                 PE3D_CUDA(cudaFuncSetAttribute(t.k[a][b], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)SMEM_BUDGET));
                 PE3D_CUDA(cudaFuncSetAttribute(t.k[a][b], cudaFuncAttributePreferredSharedMemoryCarveout, 100));
@@ -72,7 +76,7 @@ int batch_kernels(const BatchTable<C>** out) {
     return PE3D_OK;
 }
 
-inline int batch_class(int L) { return std::max(0, chunk_class(L) - 1); }
+inline int batch_class(int L) { return std::max(0, chunk_class(L)); }
 
 // Advance every march i from its current field (w of plans[i]) through steps
 // [j0[i], j1[i]) in cooperative launches of max(j1 - j0) batched steps in all:
