@@ -16,9 +16,9 @@ using namespace pe3d;
 template <typename C>
 struct BatchTable {
     const void* k[4][4];
-    // the FP64 residual correction of a batched step (FP32 marches only): one
-    // instantiation at the largest chunks, shorter chunks predicated
-    const void* refine;
+    // the FP64 residual correction of a batched step (FP32 marches only), in
+    // the same chunk classes as the march
+    const void* refine[4][4];
     BatchTable() {
 #define PE3D_B(a, b) k[a][b] = (const void*)k_march_batched<C, CHUNK_MAX[a], CHUNK_MAX[b]>
         PE3D_B(0, 0); PE3D_B(0, 1); PE3D_B(0, 2); PE3D_B(0, 3);
@@ -26,8 +26,16 @@ struct BatchTable {
         PE3D_B(2, 0); PE3D_B(2, 1); PE3D_B(2, 2); PE3D_B(2, 3);
         PE3D_B(3, 0); PE3D_B(3, 1); PE3D_B(3, 2); PE3D_B(3, 3);
 #undef PE3D_B
-        if constexpr (sizeof(C) == 8) refine = (const void*)k_refine_batched<C, CHUNK_MAX[3], CHUNK_MAX[3]>;
-        else refine = nullptr;
+        for (auto& row : refine)
+            for (auto& f : row) f = nullptr;
+        if constexpr (sizeof(C) == 8) {
+#define PE3D_R(a, b) refine[a][b] = (const void*)k_refine_batched<C, CHUNK_MAX[a], CHUNK_MAX[b]>
+            PE3D_R(0, 0); PE3D_R(0, 1); PE3D_R(0, 2); PE3D_R(0, 3);
+            PE3D_R(1, 0); PE3D_R(1, 1); PE3D_R(1, 2); PE3D_R(1, 3);
+            PE3D_R(2, 0); PE3D_R(2, 1); PE3D_R(2, 2); PE3D_R(2, 3);
+            PE3D_R(3, 0); PE3D_R(3, 1); PE3D_R(3, 2); PE3D_R(3, 3);
+#undef PE3D_R
+        }
     }
 };
 
@@ -66,10 +74,14 @@ int batch_kernels(const BatchTable<C>** out) {
                                                (int)SMEM_BUDGET));
                 PE3D_CUDA(cudaFuncSetAttribute(t.k[a][b], cudaFuncAttributePreferredSharedMemoryCarveout, 100));
             }
-        if (t.refine) {
-            PE3D_CUDA(cudaFuncSetAttribute(t.refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BUDGET));
-            PE3D_CUDA(cudaFuncSetAttribute(t.refine, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-        }
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b)
+                if (t.refine[a][b]) {
+                    PE3D_CUDA(cudaFuncSetAttribute(t.refine[a][b], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)SMEM_BUDGET));
+                    PE3D_CUDA(cudaFuncSetAttribute(t.refine[a][b], cudaFuncAttributePreferredSharedMemoryCarveout,
+                                                   100));
+                }
         mark_context_prepared(&t);
     }
     *out = &t;
@@ -160,17 +172,18 @@ int launch_batched(pe3d_plan_s* owner, std::vector<MarchArgs<C>>& descs, int nst
         PE3D_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(NT), args, smem, stream));
         owner->total_launches += 1;
         if (corr) {
-            if (!bt->refine) return fail(PE3D_ERR_ARG, "the FP64 residual correction is for FP32 marches");
+            const void* rfn = bt->refine[ca][cb];
+            if (!rfn) return fail(PE3D_ERR_ARG, "the FP64 residual correction is for FP32 marches");
             if (!grid_r) {
                 int nr = 0;
-                PE3D_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nr, bt->refine, NT, smem));
+                PE3D_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nr, rfn, NT, smem));
                 if (nr < 1) return fail(PE3D_ERR_ARG, "batched correction kernel does not fit on an SM");
                 grid_r = std::min(nr * owner->num_sms, std::max(pref[n], pref[2 * n + 1]));
             }
             PE3D_CUDA(cudaMemsetAsync(owner->bar, 0, sizeof(unsigned), stream));
             int tr = t1;
             void* rargs[] = {&dd, &nn, &dp, &tr, &bar, &status};
-            PE3D_CUDA(cudaLaunchCooperativeKernel(bt->refine, dim3(grid_r), dim3(NT), rargs, smem, stream));
+            PE3D_CUDA(cudaLaunchCooperativeKernel(rfn, dim3(grid_r), dim3(NT), rargs, smem, stream));
             owner->total_launches += 1;
         }
         t0 = te;
